@@ -1,0 +1,175 @@
+"""Plain FP64 CPU oracle for the WENO5 Teukolsky stage operator (arXiv 2010.04760).
+
+TEST INFRASTRUCTURE ONLY. Only the test suite, ``__graft_entry__.smoke()`` and
+``bench.py`` (its ``cpu_baseline`` leg and its reference arm) may import this
+package. It shares no code with the CUDA library under
+``paper_2010_04760_gb300``; the C source ``teuk_oracle.c`` cites the paper
+passage each routine follows.
+
+Layout: state ``u[4, nth, nr]`` (Psi_R, Psi_I, pi_R, pi_I); coefficients
+``coef[9, nth, nr]`` = b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth.
+Weight precision codes: 0 binary64, 1 binary32, 2 binary16, 3 bfloat16.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "teuk_oracle.c")
+_LIB = os.path.join(_HERE, "libteuk_oracle.so")
+_lib = None
+
+WPREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "f64r": 4}
+
+
+def build(force=False):
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", _LIB, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    return _LIB
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("nth", ctypes.c_int),
+                ("rs_min", ctypes.c_double), ("rs_max", ctypes.c_double),
+                ("M", ctypes.c_double), ("a", ctypes.c_double),
+                ("s", ctypes.c_int), ("m", ctypes.c_int),
+                ("eps", ctypes.c_double), ("wprec", ctypes.c_int)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        D, I, L, P = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
+        sig = {
+            "orc_rstar_of_r": (D, [D, D, D]),
+            "orc_r_of_rstar": (D, [D, D, D]),
+            "orc_coeff_point": (None, [D, D, D, D, I, I, P]),
+            "orc_coefficients": (None, [P, P]),
+            "orc_round_w": (D, [I, D]),
+            "orc_weno5_weights": (None, [I, I, P, D, P]),
+            "orc_weno5_flux": (D, [I, I, P, D, P, P, P]),
+            "orc_weno5_deriv_1d": (None, [P, I, D, I, I, D, I, P, P, P, P]),
+            "orc_rhs": (None, [P, P, P, P]),
+            "orc_rk3_step": (None, [P, P, D, P, L]),
+            "orc_rk3_linear": (None, [D, D, D, L, P]),
+            "orc_advect_1d": (None, [P, I, D, D, L, I, I, D]),
+            "orc_observe": (None, [P, P, D, P, P]),
+            "orc_num_threads": (I, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def grid(nr, nth, rs_min, rs_max, M=1.0, a=0.0, s=0, m=0, eps=1e-6, wprec="fp64"):
+    w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    return Grid(nr, nth, rs_min, rs_max, M, a, s, m, eps, w)
+
+
+def num_threads():
+    return _load().orc_num_threads()
+
+
+def rstar_of_r(r, M=1.0, a=0.0):
+    return _load().orc_rstar_of_r(r, M, a)
+
+
+def r_of_rstar(rs, M=1.0, a=0.0):
+    return _load().orc_r_of_rstar(rs, M, a)
+
+
+def coeff_point(r, th, M, a, s, m):
+    out = np.zeros(9)
+    _load().orc_coeff_point(r, th, M, a, s, m, _ptr(out))
+    return out
+
+
+def coefficients(g):
+    coef = np.zeros((9, g.nth, g.nr))
+    _load().orc_coefficients(ctypes.byref(g), _ptr(coef))
+    return coef
+
+
+def round_w(wprec, x):
+    w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    return _load().orc_round_w(w, float(x))
+
+
+def weno5_weights(f5, dir, wprec="fp64", eps=1e-6):
+    w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    f5 = _f64(f5)
+    out = np.zeros(3)
+    _load().orc_weno5_weights(w, dir, _ptr(f5), eps, _ptr(out))
+    return out
+
+
+def weno5_deriv_1d(f, h, dir, wprec="fp64", eps=1e-6, periodic=True, force_w=None,
+                   return_wq=False):
+    w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    f = _f64(f)
+    n = f.size
+    D = np.zeros(n)
+    fw = None if force_w is None else _f64(force_w)
+    wo = np.zeros((n, 3)) if return_wq else None
+    qo = np.zeros((n, 3)) if return_wq else None
+    _load().orc_weno5_deriv_1d(_ptr(f), n, h, dir, w, eps, int(periodic),
+                               None if fw is None else _ptr(fw), _ptr(D),
+                               None if wo is None else _ptr(wo),
+                               None if qo is None else _ptr(qo))
+    if return_wq:
+        return D, wo, qo
+    return D
+
+
+def rhs(g, coef, u):
+    coef, u = _f64(coef), _f64(u)
+    F = np.zeros_like(u)
+    _load().orc_rhs(ctypes.byref(g), _ptr(coef), _ptr(u), _ptr(F))
+    return F
+
+
+def rk3_step(g, coef, dt, u, nsteps=1):
+    coef = _f64(coef)
+    u = _f64(u).copy()
+    _load().orc_rk3_step(ctypes.byref(g), _ptr(coef), dt, _ptr(u), int(nsteps))
+    return u
+
+
+def rk3_linear(lam, dt, nsteps, y0=1.0 + 0.0j):
+    y = np.array([np.real(y0), np.imag(y0)], dtype=np.float64)
+    _load().orc_rk3_linear(float(np.real(lam)), float(np.imag(lam)), dt, int(nsteps), _ptr(y))
+    return complex(y[0], y[1])
+
+
+def advect_1d(f, h, dt, nsteps, dir=1, wprec="fp64", eps=1e-6):
+    w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    f = _f64(f).copy()
+    _load().orc_advect_1d(_ptr(f), f.size, h, dt, int(nsteps), dir, w, eps)
+    return f
+
+
+def observe(g, u, rs_ext):
+    u = _f64(u)
+    wave = np.zeros((g.nth, 2))
+    hor = np.zeros((g.nth, 6))
+    _load().orc_observe(ctypes.byref(g), _ptr(u), rs_ext, _ptr(wave), _ptr(hor))
+    return wave, hor

@@ -1,0 +1,486 @@
+/*
+ * Plain FP64 CPU oracle for the mixed-precision WENO5 Teukolsky stage operator
+ * of arXiv 2010.04760. TEST INFRASTRUCTURE ONLY: only the test suite,
+ * __graft_entry__.smoke() and bench.py (cpu_baseline leg, reference arm) may
+ * load it; the product (CUDA) path never does. It shares no code with the CUDA
+ * library. Every routine follows the paper's steps in the paper's order, with
+ * plain loops; the passage each one follows is cited beside it.
+ *
+ * Readings of points the paper leaves open (each is listed in the design doc):
+ *  - Coordinates: Boyer-Lindquist time t, tortoise r*, ingoing azimuth
+ *    phi~ (Sec. 2.2), in place of the hyperboloidal (tau, rho) whose
+ *    coefficients the paper does not print.
+ *  - First-order variable pi = Psi_t + b Psi_* with b = +sqrt(A**) > 0, so the
+ *    Psi rows have speed +b and the pi rows -b, as Sec. 3.1 states.
+ *  - r* boundaries: ghost values copy the edge value (zeroth-order
+ *    extrapolation). theta: cell-centred grid, ghost rows mirror across the
+ *    poles with parity (-1)^(m+s).
+ *  - theta derivatives: fourth-order centred differences (the paper says
+ *    "standard centered differencing" without an order).
+ *  - Reduced-precision weights: first differences formed in binary64, scaled
+ *    by a power of two, rounded to the weight format; smoothness indicators,
+ *    epsilon, alpha and omega computed in that format with every operation
+ *    rounded; alpha normalised by the smallest (eps + IS). omega_0, omega_2
+ *    promoted to binary64 and omega_1 = 1 - omega_0 - omega_2 there (Sec. 3.1.3).
+ *  - WENO epsilon: a parameter (1e-6 by default), unstated in the paper.
+ */
+#include <math.h>
+#include <complex.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include "teuk_oracle.h"
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tortoise coordinate, r* = int (r^2+a^2)/Delta dr (Sec. 2.2). Integration  */
+/* constant: the one that makes r* -> r + 2M ln(r/2M - 1) at a = 0.          */
+/* ------------------------------------------------------------------------ */
+double orc_rstar_of_r(double r, double M, double a) {
+    if (fabs(a) < M) {
+        double d = sqrt(M * M - a * a);
+        double rp = M + d, rm = M - d;
+        return r + (2.0 * M * rp / (rp - rm)) * log((r - rp) / (2.0 * M))
+                 - (2.0 * M * rm / (rp - rm)) * log((r - rm) / (2.0 * M));
+    }
+    /* extremal a = M: Delta = (r - M)^2 */
+    return r + 2.0 * M * log((r - M) / M) - 2.0 * M * M / (r - M);
+}
+
+/* r(r*) by bisection on the monotone map r -> r*, r in (r_+, infinity). */
+double orc_r_of_rstar(double rs, double M, double a) {
+    double rp = M + sqrt(fmax(M * M - a * a, 0.0));
+    double lo = rp, hi = rp + 1.0;
+    while (orc_rstar_of_r(hi, M, a) < rs) hi = rp + 2.0 * (hi - rp);
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double v = (mid > rp) ? orc_rstar_of_r(mid, M, a) : -INFINITY;
+        if (v < rs) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients of the first-order system (Eqs. final, evln; matrices M, A,  */
+/* L) obtained from the Teukolsky master equation (Eq. teuk0) with           */
+/* Psi = exp(i m phi~) psi(t, r*, theta):                                    */
+/*   psi_tt = A** psi_** + B* psi_* + Ath psi_thth + Bth psi_th              */
+/*            + Bt psi_t + C psi                                             */
+/* with varpi = r^2+a^2, Delta = r^2-2Mr+a^2, Sigma2 = varpi^2 -             */
+/* a^2 Delta sin^2(theta), and                                               */
+/*   A** = varpi^2/Sigma2,                                                   */
+/*   B*  = [2 r Delta + 2 i m a varpi + 2 s (r-M) varpi]/Sigma2,             */
+/*   Ath = Delta/Sigma2, Bth = Delta cot(theta)/Sigma2,                      */
+/*   Bt  = [-4 i M a m r - 2 s (r Delta - M (r^2-a^2)) - 2 i s a Delta       */
+/*          cos(theta)]/Sigma2,                                              */
+/*   C   = [4 i s m a (r-M) + Delta (s - (m + s cos)^2/sin^2)]/Sigma2.       */
+/* First-order form (Sec. 2.3): pi = psi_t + b psi_*, b = sqrt(A**), so      */
+/*   psi_t = pi - b psi_*,                                                   */
+/*   pi_t  = b pi_* + K psi_* + Ath psi_thth + Bth psi_th + Bt pi + C psi,   */
+/*   K = B* - b b_* - b Bt,  b_* = d b / d r* = (Delta/varpi) d b / d r.     */
+/* out = {b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth}.                */
+/* ------------------------------------------------------------------------ */
+void orc_coeff_point(double r, double th, double M, double a, int s, int m,
+                     double out[9]) {
+    double sn = sin(th), cs = cos(th);
+    double varpi = r * r + a * a;
+    double Delta = r * r - 2.0 * M * r + a * a;
+    double Sigma2 = varpi * varpi - a * a * Delta * sn * sn;
+    double Sigma = sqrt(Sigma2);
+
+    double complex Bstar = (2.0 * r * Delta + 2.0 * I * m * a * varpi
+                            + 2.0 * s * (r - M) * varpi) / Sigma2;
+    double Ath = Delta / Sigma2;
+    double Bth = Delta * (cs / sn) / Sigma2;
+    double complex Bt = (-4.0 * I * M * a * m * r
+                         - 2.0 * s * (r * Delta - M * (r * r - a * a))
+                         - 2.0 * I * s * a * Delta * cs) / Sigma2;
+    double mc = m + s * cs;
+    double complex C = (4.0 * I * s * m * a * (r - M)
+                        + Delta * (s - mc * mc / (sn * sn))) / Sigma2;
+
+    double b = varpi / Sigma;
+    double dSigma2_dr = 2.0 * varpi * (2.0 * r) - a * a * sn * sn * 2.0 * (r - M);
+    double db_dr = 2.0 * r / Sigma - varpi * dSigma2_dr / (2.0 * Sigma2 * Sigma);
+    double b_star = (Delta / varpi) * db_dr;
+    double complex K = Bstar - b * b_star - b * Bt;
+
+    out[0] = b;
+    out[1] = creal(K);  out[2] = cimag(K);
+    out[3] = creal(Bt); out[4] = cimag(Bt);
+    out[5] = creal(C);  out[6] = cimag(C);
+    out[7] = Ath;       out[8] = Bth;
+}
+
+/* Grid (reading): r*_i = rs_min + i h, h = (rs_max - rs_min)/(nr-1);       */
+/* theta_j = (j + 1/2) pi / nth (cell centred, never on a pole).            */
+void orc_coefficients(const orc_grid* g, double* coef) {
+    int nr = g->nr, nth = g->nth;
+    double h = (g->rs_max - g->rs_min) / (nr - 1);
+    long plane = (long)nr * nth;
+    for (int i = 0; i < nr; ++i) {
+        double r = orc_r_of_rstar(g->rs_min + i * h, g->M, g->a);
+        for (int j = 0; j < nth; ++j) {
+            double th = (j + 0.5) * M_PI / nth;
+            double c[9];
+            orc_coeff_point(r, th, g->M, g->a, g->s, g->m, c);
+            for (int k = 0; k < 9; ++k) coef[k * plane + (long)j * nr + i] = c[k];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rounding to the weight format. A value is rounded to p significant bits  */
+/* (round to nearest, ties to even), with the format's smallest normal       */
+/* exponent emin fixing the subnormal spacing and overflow going to +-inf.   */
+/* binary16: p = 11, emin = -14;  bfloat16: p = 8, emin = -126.              */
+/* One arithmetic operation done in binary64 and then rounded this way is    */
+/* the correctly rounded operation in the narrower format (53 >= 2p + 2).    */
+/* ------------------------------------------------------------------------ */
+static double round_to_format(double x, int p, int emin, double maxfinite) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e2;
+    frexp(x, &e2);                 /* |x| = f 2^e2, f in [0.5, 1) */
+    int E = e2 - 1;                /* floor(log2 |x|) */
+    if (E < emin) E = emin;        /* subnormal: fixed spacing 2^(emin-p+1) */
+    double q = nearbyint(ldexp(x, p - 1 - E));   /* ties to even */
+    double y = ldexp(q, E - (p - 1));
+    if (fabs(y) > maxfinite) return copysign(INFINITY, x);
+    return y;
+}
+
+double orc_round_w(int wprec, double x) {
+    switch (wprec) {
+    case 1: return (double)(float)x;
+    case 2: return round_to_format(x, 11, -14, 65504.0);
+    case 3: return round_to_format(x, 8, -126, ldexp(255.0, 120));
+    default: return x;
+    }
+}
+
+/* Range limits of the scaled epsilon (reading): eps_hat is clamped to       */
+/* [tiny, huge] before rounding; both are powers of two.                     */
+static void eps_range(int wprec, double* tiny, double* huge) {
+    if (wprec == 2)      { *tiny = ldexp(1.0, -14);   *huge = ldexp(1.0, 15); }
+    else if (wprec == 4) { *tiny = ldexp(1.0, -1022); *huge = ldexp(1.0, 1000); }
+    else                 { *tiny = ldexp(1.0, -126);  *huge = ldexp(1.0, 100); }
+}
+
+/* ------------------------------------------------------------------------ */
+/* WENO5 nonlinear weights (Sec. 3.1.2).                                     */
+/* dir = +1: f5 = f_{j-2..j+2}, weights of the positive-direction flux at    */
+/*           j+1/2; dir = -1: f5 = f_{j-1..j+3}, negative-direction flux.    */
+/* w[k] = omega_k with the paper's indexing (omega^-_0 belongs to the        */
+/* stencil f_{j+1}, f_{j+2}, f_{j+3}).                                       */
+/* ------------------------------------------------------------------------ */
+static const double D_LIN[3] = {0.1, 0.6, 0.3};
+
+static void weights_fp64(int dir, const double* f, double eps, double w[3]) {
+    double IS[3];
+    if (dir > 0) {
+        IS[0] = 13.0 / 12.0 * pow(f[0] - 2 * f[1] + f[2], 2)
+              + 0.25 * pow(f[0] - 4 * f[1] + 3 * f[2], 2);
+        IS[1] = 13.0 / 12.0 * pow(f[1] - 2 * f[2] + f[3], 2)
+              + 0.25 * pow(f[1] - f[3], 2);
+        IS[2] = 13.0 / 12.0 * pow(f[2] - 2 * f[3] + f[4], 2)
+              + 0.25 * pow(3 * f[2] - 4 * f[3] + f[4], 2);
+    } else {
+        IS[0] = 13.0 / 12.0 * pow(f[2] - 2 * f[3] + f[4], 2)
+              + 0.25 * pow(3 * f[2] - 4 * f[3] + f[4], 2);
+        IS[1] = 13.0 / 12.0 * pow(f[1] - 2 * f[2] + f[3], 2)
+              + 0.25 * pow(f[1] - f[3], 2);
+        IS[2] = 13.0 / 12.0 * pow(f[0] - 2 * f[1] + f[2], 2)
+              + 0.25 * pow(f[0] - 4 * f[1] + 3 * f[2], 2);
+    }
+    double alpha[3], sum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        alpha[k] = D_LIN[k] / pow(eps + IS[k], 2);
+        sum += alpha[k];
+    }
+    for (int k = 0; k < 3; ++k) w[k] = alpha[k] / sum;
+}
+
+/* Reduced-precision weights (Sec. 3.1.3, reading above). The smoothness     */
+/* indicators are the paper's, written with the stencil's first differences */
+/* x: for dir = +1, x_k = f_{k+1} - f_k over f_{j-2..j+2}, and              */
+/*   f_{j-2}-2f_{j-1}+f_j = x1-x0,   f_{j-2}-4f_{j-1}+3f_j = 3x1-x0,         */
+/*   f_{j-1}-2f_j+f_{j+1} = x2-x1,   f_{j-1}-f_{j+1}      = -(x1+x2),        */
+/*   f_j-2f_{j+1}+f_{j+2} = x3-x2,   3f_j-4f_{j+1}+f_{j+2} = x3-3x2.         */
+/* For dir = -1 the same identities hold with the first differences taken   */
+/* in reverse order (the negative-direction stencil is the mirror image).    */
+static void weights_reduced(int wprec, int dir, const double* f, double eps,
+                            double w[3]) {
+    double x[4];
+    for (int k = 0; k < 4; ++k) x[k] = f[k + 1] - f[k];      /* binary64 */
+    if (dir < 0) {                                           /* mirror */
+        double t0 = x[0], t1 = x[1];
+        x[0] = x[3]; x[1] = x[2]; x[2] = t1; x[3] = t0;
+    }
+    double mx = 0.0;
+    for (int k = 0; k < 4; ++k) mx = fmax(mx, fabs(x[k]));
+    int e = 0;
+    if (mx > 0.0) { int e2; frexp(mx, &e2); e = e2 - 1; }   /* 2^e <= mx < 2^(e+1) */
+
+#define RW(v) orc_round_w(wprec, (v))
+    double xh[4];
+    for (int k = 0; k < 4; ++k) xh[k] = RW(ldexp(x[k], -e));
+    double tiny, huge;
+    eps_range(wprec, &tiny, &huge);
+    double eh = ldexp(eps, -2 * e);
+    if (eh < tiny) eh = tiny;
+    if (eh > huge) eh = huge;
+    eh = RW(eh);
+    double c13 = RW(13.0 / 12.0), c14 = 0.25, d[3];
+    for (int k = 0; k < 3; ++k) d[k] = RW(D_LIN[k]);
+
+    double a, b, IS[3];
+    a = RW(xh[1] - xh[0]);             b = RW(RW(3.0 * xh[1]) - xh[0]);
+    IS[0] = RW(RW(c13 * RW(a * a)) + RW(c14 * RW(b * b)));
+    a = RW(xh[2] - xh[1]);             b = RW(xh[1] + xh[2]);
+    IS[1] = RW(RW(c13 * RW(a * a)) + RW(c14 * RW(b * b)));
+    a = RW(xh[3] - xh[2]);             b = RW(RW(3.0 * xh[2]) - xh[3]);
+    IS[2] = RW(RW(c13 * RW(a * a)) + RW(c14 * RW(b * b)));
+
+    double t[3], tmin, alpha[3];
+    for (int k = 0; k < 3; ++k) t[k] = RW(eh + IS[k]);
+    tmin = fmin(t[0], fmin(t[1], t[2]));
+    for (int k = 0; k < 3; ++k) {
+        double rk = RW(tmin / t[k]);
+        alpha[k] = RW(d[k] * RW(rk * rk));
+    }
+    double sum = RW(RW(alpha[0] + alpha[1]) + alpha[2]);
+    for (int k = 0; k < 3; ++k) w[k] = RW(alpha[k] / sum);
+#undef RW
+}
+
+void orc_weno5_weights(int wprec, int dir, const double* f5, double eps,
+                       double w[3]) {
+    if (wprec == 0) weights_fp64(dir, f5, eps, w);
+    else weights_reduced(wprec, dir, f5, eps, w);
+}
+
+/* Numerical flux at j+1/2 from the candidate stencils (Sec. 3.1.2). With    */
+/* reduced weights, omega_1 = 1 - omega_0 - omega_2 in binary64 so that the  */
+/* weights sum to one in the high precision (Sec. 3.1.3).                    */
+double orc_weno5_flux(int wprec, int dir, const double* f, double eps,
+                      const double* force_w, double w_out[3], double q_out[3]) {
+    double w[3], q[3];
+    if (force_w) { w[0] = force_w[0]; w[1] = force_w[1]; w[2] = force_w[2]; }
+    else orc_weno5_weights(wprec, dir, f, eps, w);
+    if (!force_w && wprec != 0) w[1] = 1.0 - w[0] - w[2];
+    if (dir > 0) {
+        q[0] = (2.0 * f[0] - 7.0 * f[1] + 11.0 * f[2]) / 6.0;
+        q[1] = (-f[1] + 5.0 * f[2] + 2.0 * f[3]) / 6.0;
+        q[2] = (2.0 * f[2] + 5.0 * f[3] - f[4]) / 6.0;
+    } else {
+        q[2] = (-f[0] + 5.0 * f[1] + 2.0 * f[2]) / 6.0;
+        q[1] = (2.0 * f[1] + 5.0 * f[2] - f[3]) / 6.0;
+        q[0] = (11.0 * f[2] - 7.0 * f[3] + 2.0 * f[4]) / 6.0;
+    }
+    if (w_out) { w_out[0] = w[0]; w_out[1] = w[1]; w_out[2] = w[2]; }
+    if (q_out) { q_out[0] = q[0]; q_out[1] = q[1]; q_out[2] = q[2]; }
+    return w[0] * q[0] + w[1] * q[1] + w[2] * q[2];
+}
+
+/* Derivative of one line, D_i = (fhat_{i+1/2} - fhat_{i-1/2}) / h           */
+/* (Sec. 3.1.2). Ghosts: periodic wrap, or copies of the edge value.         */
+/* w_out / q_out (optional, 3 per interface) receive the weights and          */
+/* candidate values of interface i+1/2 for i = 0..n-1.                       */
+void orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
+                        double eps, int periodic, const double* force_w,
+                        double* D, double* w_out, double* q_out) {
+    double* ext = (double*)malloc(sizeof(double) * (n + 6));
+    double* fh = (double*)malloc(sizeof(double) * (n + 1));
+    for (int k = -3; k < n + 3; ++k) {
+        int src = k;
+        if (periodic) src = ((k % n) + n) % n;
+        else src = k < 0 ? 0 : (k >= n ? n - 1 : k);
+        ext[k + 3] = f[src];
+    }
+    /* interface i+1/2 for i = -1 .. n-1, stored at fh[i+1] */
+    for (int i = -1; i < n; ++i) {
+        const double* st = (dir > 0) ? &ext[i - 2 + 3] : &ext[i - 1 + 3];
+        double wl[3], ql[3];
+        fh[i + 1] = orc_weno5_flux(wprec, dir, st, eps, force_w, wl, ql);
+        if (i >= 0 && w_out) for (int k = 0; k < 3; ++k) w_out[3 * i + k] = wl[k];
+        if (i >= 0 && q_out) for (int k = 0; k < 3; ++k) q_out[3 * i + k] = ql[k];
+    }
+    for (int i = 0; i < n; ++i) D[i] = (fh[i + 1] - fh[i]) / h;
+    free(ext);
+    free(fh);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Right-hand side F(u) of du/dt = F(u) = -(M du/dr* + L u + A u)            */
+/* (Eq. evln). Psi components take the positive-direction WENO flux, pi      */
+/* components the negative-direction one, by the sign of M's diagonal        */
+/* (Sec. 3.1.2); m31, m32 use the same Psi derivative. theta derivatives are */
+/* fourth-order centred with parity ghosts. Complex form:                    */
+/*   F_Psi = pi - b D_Psi,                                                   */
+/*   F_pi  = b D_pi + K D_Psi + Ath Psi_thth + Bth Psi_th + Bt pi + C Psi.   */
+/* ------------------------------------------------------------------------ */
+void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) {
+    int nr = g->nr, nth = g->nth;
+    long plane = (long)nr * nth;
+    double h = (g->rs_max - g->rs_min) / (nr - 1);
+    double dth = M_PI / nth;
+    double sigma = ((g->m + g->s) % 2 == 0) ? 1.0 : -1.0;
+
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < nth; ++j) {
+        double* Dc = (double*)malloc(sizeof(double) * 4 * nr);
+        for (int c = 0; c < 4; ++c) {
+            int dir = (c < 2) ? +1 : -1;
+            orc_weno5_deriv_1d(&u[c * plane + (long)j * nr], nr, h, dir, g->wprec,
+                               g->eps, 0, NULL, &Dc[c * nr], NULL, NULL);
+        }
+        /* rows j-2 .. j+2 of Psi, with ghosts across the poles */
+        int rows[5];
+        double sgn[5];
+        for (int k = -2; k <= 2; ++k) {
+            int jj = j + k;
+            double sg = 1.0;
+            if (jj < 0) { jj = -1 - jj; sg = sigma; }
+            if (jj >= nth) { jj = 2 * nth - 1 - jj; sg = sigma; }
+            rows[k + 2] = jj;
+            sgn[k + 2] = sg;
+        }
+        for (int i = 0; i < nr; ++i) {
+            long p = (long)j * nr + i;
+            double complex psi = u[0 * plane + p] + I * u[1 * plane + p];
+            double complex pi = u[2 * plane + p] + I * u[3 * plane + p];
+            double complex Dpsi = Dc[0 * nr + i] + I * Dc[1 * nr + i];
+            double complex Dpi = Dc[2 * nr + i] + I * Dc[3 * nr + i];
+            double complex nb[5];
+            for (int k = 0; k < 5; ++k) {
+                long q = (long)rows[k] * nr + i;
+                nb[k] = sgn[k] * (u[0 * plane + q] + I * u[1 * plane + q]);
+            }
+            double complex psi_th = (nb[0] - 8.0 * nb[1] + 8.0 * nb[3] - nb[4])
+                                    / (12.0 * dth);
+            double complex psi_thth = (-nb[0] + 16.0 * nb[1] - 30.0 * nb[2]
+                                       + 16.0 * nb[3] - nb[4]) / (12.0 * dth * dth);
+            double b = coef[0 * plane + p];
+            double complex K = coef[1 * plane + p] + I * coef[2 * plane + p];
+            double complex Bt = coef[3 * plane + p] + I * coef[4 * plane + p];
+            double complex C = coef[5 * plane + p] + I * coef[6 * plane + p];
+            double Ath = coef[7 * plane + p], Bth = coef[8 * plane + p];
+
+            double complex Fpsi = pi - b * Dpsi;
+            double complex Fpi = b * Dpi + K * Dpsi + Ath * psi_thth
+                                 + Bth * psi_th + Bt * pi + C * psi;
+            F[0 * plane + p] = creal(Fpsi);
+            F[1 * plane + p] = cimag(Fpsi);
+            F[2 * plane + p] = creal(Fpi);
+            F[3 * plane + p] = cimag(Fpi);
+        }
+        free(Dc);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* SSP-RK(3,3) in Shu-Osher form (Sec. 3.2):                                 */
+/*   u1 = u + dt F(u); u2 = 3/4 u + 1/4 (u1 + dt F(u1));                     */
+/*   u^{n+1} = 1/3 u + 2/3 (u2 + dt F(u2)).                                  */
+/* One routine serves the PDE and the scalar test equation.                  */
+/* ------------------------------------------------------------------------ */
+typedef void (*rhs_fn)(const void* ctx, const double* u, double* F);
+
+static void ssprk3(long n, double* u, double dt, long nsteps, rhs_fn rhs,
+                   const void* ctx) {
+    double* u1 = (double*)malloc(sizeof(double) * n);
+    double* u2 = (double*)malloc(sizeof(double) * n);
+    double* Fv = (double*)malloc(sizeof(double) * n);
+    for (long step = 0; step < nsteps; ++step) {
+        rhs(ctx, u, Fv);
+        for (long k = 0; k < n; ++k) u1[k] = u[k] + dt * Fv[k];
+        rhs(ctx, u1, Fv);
+        for (long k = 0; k < n; ++k)
+            u2[k] = 0.75 * u[k] + 0.25 * (u1[k] + dt * Fv[k]);
+        rhs(ctx, u2, Fv);
+        for (long k = 0; k < n; ++k)
+            u[k] = u[k] / 3.0 + 2.0 / 3.0 * (u2[k] + dt * Fv[k]);
+    }
+    free(u1);
+    free(u2);
+    free(Fv);
+}
+
+typedef struct { const orc_grid* g; const double* coef; } pde_ctx;
+
+static void pde_rhs(const void* ctx, const double* u, double* F) {
+    const pde_ctx* c = (const pde_ctx*)ctx;
+    orc_rhs(c->g, c->coef, u, F);
+}
+
+void orc_rk3_step(const orc_grid* g, const double* coef, double dt, double* u,
+                  long nsteps) {
+    pde_ctx c = {g, coef};
+    ssprk3(4L * g->nr * g->nth, u, dt, nsteps, pde_rhs, &c);
+}
+
+typedef struct { double lr, li; } lin_ctx;
+
+static void lin_rhs(const void* ctx, const double* y, double* F) {
+    const lin_ctx* c = (const lin_ctx*)ctx;
+    F[0] = c->lr * y[0] - c->li * y[1];
+    F[1] = c->lr * y[1] + c->li * y[0];
+}
+
+/* y' = lambda y for complex lambda; y = {Re, Im}. */
+void orc_rk3_linear(double lam_re, double lam_im, double dt, long nsteps,
+                    double y[2]) {
+    lin_ctx c = {lam_re, lam_im};
+    ssprk3(2, y, dt, nsteps, lin_rhs, &c);
+}
+
+typedef struct { int n, dir, wprec; double h, eps; } adv_ctx;
+
+static void adv_rhs(const void* ctx, const double* u, double* F) {
+    const adv_ctx* c = (const adv_ctx*)ctx;
+    orc_weno5_deriv_1d(u, c->n, c->h, c->dir, c->wprec, c->eps, 1, NULL, F,
+                       NULL, NULL);
+    for (int i = 0; i < c->n; ++i) F[i] = -(double)c->dir * F[i];
+}
+
+/* Periodic linear advection u_t + dir u_x = 0 with the dir-upwinded flux.   */
+void orc_advect_1d(double* f, int n, double h, double dt, long nsteps, int dir,
+                   int wprec, double eps) {
+    adv_ctx c = {n, dir, wprec, h, eps};
+    ssprk3(n, f, dt, nsteps, adv_rhs, &c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observation (Sec. 4): Psi along theta at the r* node nearest rs_ext, and  */
+/* at the innermost node Psi, pi and dPsi/dr* (one-sided second order).      */
+/* wave[2j+{0,1}] = Psi; horizon[6j + {0..5}] = Psi, pi, Psi_*.              */
+/* ------------------------------------------------------------------------ */
+void orc_observe(const orc_grid* g, const double* u, double rs_ext, double* wave,
+                 double* horizon) {
+    int nr = g->nr, nth = g->nth;
+    long plane = (long)nr * nth;
+    double h = (g->rs_max - g->rs_min) / (nr - 1);
+    long ie = lround((rs_ext - g->rs_min) / h);
+    if (ie < 0) ie = 0;
+    if (ie > nr - 1) ie = nr - 1;
+    for (int j = 0; j < nth; ++j) {
+        long row = (long)j * nr;
+        wave[2 * j] = u[0 * plane + row + ie];
+        wave[2 * j + 1] = u[1 * plane + row + ie];
+        for (int c = 0; c < 4; ++c) horizon[6 * j + c] = u[c * plane + row];
+        for (int c = 0; c < 2; ++c) {
+            const double* f = &u[c * plane + row];
+            horizon[6 * j + 4 + c] = (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * h);
+        }
+    }
+}

@@ -1,0 +1,236 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: stencils
+derived by hand from the paper's printed formulas (tests/golden), polynomial
+exactness, convergence orders, the SSP-RK(3,3) stability polynomial, an
+independent sympy derivation of the coefficients from Eq. teuk0, the
+Regge-Wheeler potential, the spin-weighted harmonic eigenvalue relation, the
+paper's printed real matrices M, A, L, and Price's late-time tail.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2010_04760_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------------
+# Rounding to the weight formats
+# --------------------------------------------------------------------------
+def test_round_w_matches_numpy_and_torch():
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.integers(-9, 5, 2000),
+                        [0.0, 65504.0, 65519.9, 65520.0, 2.0 ** -24, 3 * 2.0 ** -26,
+                         2.0 ** -25, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11]])
+    for v in x:
+        assert o.round_w("fp32", v) == float(np.float32(v))
+        ref16 = float(np.float16(v))
+        got16 = o.round_w("fp16", v)
+        assert got16 == ref16 or (np.isinf(got16) and np.isinf(ref16)), v
+    torch = pytest.importorskip("torch")
+    xf = x.astype(np.float32).astype(np.float64)      # exactly representable in binary32
+    ref = torch.tensor(xf, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([o.round_w("bf16", v) for v in xf])
+    np.testing.assert_array_equal(got, ref)
+
+
+# --------------------------------------------------------------------------
+# Tortoise coordinate (Sec. 2.2)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("a", [0.0, 0.5, 0.999, 1.0])
+def test_tortoise_derivative_and_inverse(a):
+    M = 1.0
+    rp = M + np.sqrt(max(M * M - a * a, 0.0))
+    for r in rp + np.array([0.05, 0.3, 1.0, 4.0, 40.0, 300.0]):
+        hstep = 1e-5 * r
+        num = (o.rstar_of_r(r + hstep, M, a) - o.rstar_of_r(r - hstep, M, a)) / (2 * hstep)
+        exact = (r * r + a * a) / (r * r - 2 * M * r + a * a)
+        assert abs(num / exact - 1.0) < 1e-7
+        rs = o.rstar_of_r(r, M, a)
+        assert abs(o.r_of_rstar(rs, M, a) - r) < 1e-12 * r
+
+
+def test_tortoise_schwarzschild_lambert_w():
+    from scipy.special import lambertw
+    for rs in [-60.0, -10.0, 0.0, 3.0, 50.0, 250.0]:
+        r_exact = 2.0 * (1.0 + lambertw(np.exp(rs / 2.0 - 1.0)).real)
+        assert abs(o.r_of_rstar(rs, 1.0, 0.0) - r_exact) < 1e-12 * r_exact
+
+
+# --------------------------------------------------------------------------
+# WENO5 (Sec. 3.1.2)
+# --------------------------------------------------------------------------
+def _stencil_from_impulses(dir, length, deriv):
+    n = 32
+    coeffs = []
+    for k in range(length):
+        f = np.zeros(n)
+        i0 = 12
+        off = (-3 if dir > 0 else -2) if deriv else (-2 if dir > 0 else -1)
+        f[i0 + off + k] = 1.0
+        D = o.weno5_deriv_1d(f, 1.0, dir, periodic=True, force_w=[0.1, 0.6, 0.3],
+                             return_wq=False)
+        coeffs.append(D[i0] * 60.0)
+    return coeffs
+
+
+def test_linear_weights_reproduce_golden_stencils():
+    rows = {r[0]: [int(v) for v in r[1:]] for r in _golden_rows("weno5_linear_stencils.txt")}
+    assert np.allclose(_stencil_from_impulses(+1, 6, True), rows["deriv_plus"], atol=1e-12)
+    assert np.allclose(_stencil_from_impulses(-1, 6, True), rows["deriv_minus"], atol=1e-12)
+    # interface values: f-hat with omega = d over unit impulses
+    for dir, key in [(+1, "flux_plus"), (-1, "flux_minus")]:
+        got = []
+        for k in range(5):
+            f5 = np.zeros(5)
+            f5[k] = 1.0
+            w = np.array([0.1, 0.6, 0.3])
+            fl = o._load().orc_weno5_flux(0, dir, o._ptr(f5), 1e-6, o._ptr(w), None, None)
+            got.append(fl * 60.0)
+        assert np.allclose(got, rows[key], atol=1e-12)
+
+
+@pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16", "bf16", "f64r"])
+@pytest.mark.parametrize("dir", [1, -1])
+def test_linear_data_gives_linear_weights(wprec, dir):
+    u = {"fp64": 2.0 ** -53, "f64r": 2.0 ** -53, "fp32": 2.0 ** -24, "fp16": 2.0 ** -11,
+         "bf16": 2.0 ** -8}[wprec]
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        c0, c1 = rng.standard_normal(2) * 10.0 ** rng.integers(-3, 4, 2)
+        f5 = c0 + c1 * np.arange(5)
+        w = o.weno5_weights(f5, dir, wprec)
+        # first differences carry the binary64 cancellation error u64 |f| / |c1|
+        tol = 8 * u + 64 * 2.0 ** -53 * (1.0 + np.max(np.abs(f5)) / abs(c1))
+        assert np.all(np.abs(w - [0.1, 0.6, 0.3]) <= tol), (w, wprec)
+
+
+@pytest.mark.parametrize("dir", [1, -1])
+def test_linear_scheme_exact_to_degree_five(dir):
+    n, h = 40, 0.1
+    x = np.arange(n) * h
+    for deg in range(6):
+        f = (x - 1.3) ** deg
+        D = o.weno5_deriv_1d(f, h, dir, periodic=False, force_w=[0.1, 0.6, 0.3])
+        ex = deg * (x - 1.3) ** (deg - 1) if deg else 0 * x
+        sl = slice(4, n - 4)
+        assert np.max(np.abs(D[sl] - ex[sl])) < 1e-9 * max(1, np.max(np.abs(ex[sl])))
+    f = (x - 1.3) ** 6
+    D = o.weno5_deriv_1d(f, h, dir, periodic=False, force_w=[0.1, 0.6, 0.3])
+    assert np.max(np.abs(D[4:n - 4] - 6 * (x[4:n - 4] - 1.3) ** 5)) > 1e-6
+
+
+@pytest.mark.parametrize("dir", [1, -1])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_each_candidate_stencil_exact_to_degree_three(dir, k):
+    n, h = 40, 0.1
+    x = np.arange(n) * h
+    w = np.zeros(3)
+    w[k] = 1.0
+    for deg in range(4):
+        f = (x - 0.7) ** deg
+        D = o.weno5_deriv_1d(f, h, dir, periodic=False, force_w=w)
+        ex = deg * (x - 0.7) ** (deg - 1) if deg else 0 * x
+        assert np.max(np.abs(D[4:n - 4] - ex[4:n - 4])) < 1e-9
+    f = (x - 0.7) ** 4
+    D = o.weno5_deriv_1d(f, h, dir, periodic=False, force_w=w)
+    assert np.max(np.abs(D[4:n - 4] - 4 * (x[4:n - 4] - 0.7) ** 3)) > 1e-5
+
+
+def test_smooth_weights_approach_linear_weights_at_second_order():
+    devs = []
+    for n in (64, 128, 256):
+        h = 1.0 / n
+        x = np.arange(n) * h
+        f = np.sin(2 * np.pi * x)
+        _, w, _ = o.weno5_deriv_1d(f, h, 1, periodic=True, return_wq=True)
+        xm = x + 0.5 * h
+        mask = np.abs(np.cos(2 * np.pi * xm)) > 0.3            # away from critical points
+        devs.append(np.max(np.abs(w[mask] - [0.1, 0.6, 0.3])))
+    orders = np.log2(np.array(devs[:-1]) / np.array(devs[1:]))
+    assert np.all(orders > 1.8), (devs, orders)
+
+
+@pytest.mark.parametrize("dir", [1, -1])
+def test_fifth_order_convergence_on_periodic_advection(dir):
+    errs = []
+    for n in (40, 80, 160):
+        h = 1.0 / n
+        x = np.arange(n) * h
+        T = 0.25
+        ns = int(np.ceil(T / (0.4 * h ** (5.0 / 3.0))))
+        f = o.advect_1d(np.sin(2 * np.pi * x), h, T / ns, ns, dir=dir)
+        errs.append(np.mean(np.abs(f - np.sin(2 * np.pi * (x - dir * T)))))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 4.7), orders
+
+
+@pytest.mark.parametrize("wprec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("dir", [1, -1])
+def test_reduced_weights_within_rounding_of_fp64_weights(wprec, dir):
+    """The reduced-precision reading differs from the paper's binary64 weights
+    by a few units of the weight format's rounding, at every scale; the flux
+    difference obeys |fhat_W - fhat_64| <= sum_k |dw_k| |q_k - q_1|."""
+    u = {"fp32": 2.0 ** -24, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8}[wprec]
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for trial in range(3000):
+        scale = 10.0 ** rng.uniform(-12, 8)
+        f5 = rng.standard_normal(5) * scale
+        if trial % 3 == 0:                       # smooth-ish stencils
+            f5 = scale * (rng.standard_normal() + rng.standard_normal() * np.arange(5)
+                          + 0.01 * rng.standard_normal(5))
+        w64 = o.weno5_weights(f5, dir, "fp64")
+        wW = o.weno5_weights(f5, dir, wprec)
+        dw = np.abs(wW - w64)
+        worst = max(worst, np.max(dw) / u)
+        lib = o._load()
+        wo, qo = np.zeros(3), np.zeros(3)
+        fW = lib.orc_weno5_flux(o.WPREC[wprec], dir, o._ptr(f5), 1e-6, None, o._ptr(wo), o._ptr(qo))
+        f64 = lib.orc_weno5_flux(0, dir, o._ptr(f5), 1e-6, None, None, None)
+        bound = np.sum(np.abs(wo - w64) * np.abs(qo - qo[1])) + 1e-13 * np.max(np.abs(f5))
+        assert abs(fW - f64) <= bound, (f5, fW, f64, bound)
+    assert worst < 12.0, worst
+
+
+def test_reduced_reading_in_binary64_equals_paper_formula():
+    rng = np.random.default_rng(11)
+    for dir in (1, -1):
+        for _ in range(2000):
+            f5 = rng.standard_normal(5) * 10.0 ** rng.uniform(-10, 6)
+            assert np.max(np.abs(o.weno5_weights(f5, dir, "f64r")
+                                 - o.weno5_weights(f5, dir, "fp64"))) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# SSP-RK(3,3) (Sec. 3.2)
+# --------------------------------------------------------------------------
+def test_ssprk33_stability_polynomial():
+    c = [float(Fraction(v)) for v in _golden_rows("ssprk33_stability.txt")[0]]
+    for z in [0.3, -1.2, 0.7j, -0.4 + 1.1j, 2.0 - 0.5j]:
+        R = sum(ck * z ** k for k, ck in enumerate(c))
+        assert abs(o.rk3_linear(z, 1.0, 1) - R) < 1e-14 * max(1, abs(R))
+
+
+def test_ssprk33_third_order():
+    lam = -0.8 + 2.0j
+    errs = []
+    for ns in (20, 40, 80):
+        errs.append(abs(o.rk3_linear(lam, 1.0 / ns, ns) - np.exp(lam)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 3.0) < 0.15), orders
