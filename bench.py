@@ -1,0 +1,327 @@
+"""Benchmark: WENO5 Teukolsky point-stage updates/s, mixed vs binary64 weights.
+
+Workload: the near-extremal gravitational evolution, Kerr a = 0.999 M,
+s = -2, m = 2, grid 2048 (r* in [-100, 300] M) x 128 (theta), seeded Gaussian
+l = 2 pulse at r* = 30 M (width 3 M). A step is one SSP-RK(3,3) step: three
+fused stage launches over all 262,144 nodes (786,432 point-stage updates).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Timing: W untimed warm-up steps, then K timed steps; before each timed step a
+256 MiB buffer is written to flush the 129 MB L2 (the workload's state and
+coefficients, ~50 MB, would otherwise stay L2-resident), and each step is
+bracketed by CUDA events on the launching stream. Max over ranks. With N > 1
+(torchrun) every rank evolves its own replica (no data exchange; weak scaling).
+The reference arm (--impl reference) times the CPU oracle on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2010_04760_gb300 import inputs as I  # noqa: E402
+
+WL = I.KERR_GRAV
+METRIC = "WENO5 Teukolsky point-stage updates/s, mixed vs FP64 weights, at stated L2 err"
+UNIT = "point-stage updates/s"
+POINTS = WL.nr * WL.nth
+# binary64 flops per point-stage of the fused stage (FMA = 2), averaged over
+# the three SSP-RK(3,3) stages: first differences 4, third differences 12,
+# weighted fluxes 24, derivatives 12, Psi rows 8, pi rows 44, RK combination
+# 0/12/12 -> (104 + 116 + 116) / 3.
+FP64_FLOPS_PER_PT_STAGE = 112.0
+# algorithmic HBM bytes per point-stage: 11 coefficient planes (88 B), u_prev
+# (32 B), u_out (32 B), u^n in stages 2 and 3 (2/3 x 32 B).
+BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
+# FP64 FMA throughput measured on this GPU type (lane-FMA/s x 2 flops); the
+# nominal figure is 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS_MEASURED = 1.013
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[3:]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_init(gpus):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_gpu_steps(T, torch, wprec, steps, warmup, stream, flush):
+    """Device time of `steps` RK steps of the workload with weights `wprec`."""
+    p = T.params_from_workload(WL, wprec=wprec)
+    h = T.teuk_create(p, stream)
+    T.teuk_set_state(h, I.initial_data(WL), 0.0)
+    for _ in range(warmup):
+        T.teuk_step(h, 1)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.nvtx.range_push(f"{wprec}_timed")
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))                 # write > L2 between timed steps
+            ev[k][0].record(stream)
+            T.teuk_step(h, 1)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    assert T.teuk_check_finite(h) == T.TEUK_OK
+    h.close()
+    return sum(ms), ms
+
+
+def waveform_error(T, torch, stream, nsteps=3000):
+    """Relative L2 difference of the waveform (Psi at r* = 100 M over all theta,
+    sampled every 100 steps) between binary32 and binary64 weights."""
+    waves = {}
+    for wprec in ("fp64", "fp32"):
+        h = T.teuk_create(T.params_from_workload(WL, wprec=wprec), stream)
+        T.teuk_set_state(h, I.initial_data(WL), 0.0)
+        ws = []
+        for _ in range(nsteps // 100):
+            T.teuk_step(h, 100)
+            ws.append(T.teuk_observe(h, 100.0)[0].copy())
+        _, dt, t = T.teuk_get_info(h)
+        h.close()
+        waves[wprec] = np.array(ws)
+    err = np.linalg.norm(waves["fp32"] - waves["fp64"]) / np.linalg.norm(waves["fp64"])
+    return float(err), t
+
+
+def time_e2e(T, torch, steps, stream):
+    """Same metric through the public handle API with host buffers: every step
+    copies the state in from pinned host memory, advances one step and reads
+    the state back."""
+    p = T.params_from_workload(WL)
+    h = T.teuk_create(p, stream)
+    u_in = torch.empty((4, WL.nth, WL.nr), dtype=torch.float64, pin_memory=True).numpy()
+    u_in[...] = I.initial_data(WL)
+    u_out = torch.empty_like(torch.from_numpy(u_in)).pin_memory().numpy()
+    T.teuk_set_state(h, u_in, 0.0)
+    T.teuk_step(h, 1)
+    T.teuk_get_state(h, u_out)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        T.teuk_set_state(h, u_in, 0.0)
+        T.teuk_step(h, 1)
+        T.teuk_get_state(h, u_out)
+    el = time.perf_counter() - t0
+    h.close()
+    nbytes = u_in.nbytes
+    return el, nbytes
+
+
+def oracle_rate(nsteps_budget_s=12.0, wprec="fp32", max_steps=400):
+    """Oracle point-stage updates/s on the workload, over a bounded number of
+    RK steps chosen to take about nsteps_budget_s seconds."""
+    import oracle as o
+    g = o.grid(WL.nr, WL.nth, WL.rs_min, WL.rs_max, WL.M, WL.a, WL.s, WL.m, WL.eps, wprec)
+    co = o.coefficients(g)
+    u = I.initial_data(WL)
+    dt = 0.005
+    t0 = time.perf_counter()
+    u = o.rk3_step(g, co, dt, u, 1)
+    t1 = time.perf_counter() - t0
+    n = int(max(2, min(max_steps, nsteps_budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    u = o.rk3_step(g, co, dt, u, n)
+    el = time.perf_counter() - t0
+    return POINTS * 3 * n / el, n, el, o.num_threads()
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle on the host cores, one SSP-RK(3,3) step of the workload
+    per timed step (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle as o
+    o.build()
+    g = o.grid(WL.nr, WL.nth, WL.rs_min, WL.rs_max, WL.M, WL.a, WL.s, WL.m, WL.eps, "fp32")
+    co = o.coefficients(g)
+    u = I.initial_data(WL)
+    dt = 0.005
+    u = o.rk3_step(g, co, dt, u, args.warmup)
+    t0 = time.perf_counter()
+    u = o.rk3_step(g, co, dt, u, args.steps)
+    el = time.perf_counter() - t0
+    value = POINTS * 3 * args.steps / el
+    cores = o.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "weights_dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WL.name, "nr": WL.nr, "ntheta": WL.nth, "wprec": "fp32"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} RK steps of the {WL.nr}x{WL.nth} workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_2010_04760_gb300 as T
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    T.lib()
+    stream = torch.cuda.Stream(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    # binary64-weight baseline on the same workload
+    barrier(world)
+    ms64, _ = time_gpu_steps(T, torch, "fp64", args.steps, args.warmup, stream, flush)
+    ms64 = max_over_ranks(ms64, world, device)
+    # mixed precision (binary32 weights): the headline
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms32, per = time_gpu_steps(T, torch, "fp32", args.steps, args.warmup, stream, flush)
+    ms32 = max_over_ranks(ms32, world, device)
+    barrier(world)
+    e2e_s, nbytes = time_e2e(T, torch, max(10, args.steps // 4), stream)
+    e2e_steps = max(10, args.steps // 4)
+    e2e_s = max_over_ranks(e2e_s, world, device)
+    err, t_err = waveform_error(T, torch, stream) if rank == 0 else (None, None)
+
+    pts = POINTS * 3 * args.steps * world
+    value = pts / (ms32 * 1e-3)
+    value64 = pts / (ms64 * 1e-3)
+    launch_ms = ms32 / (3 * args.steps)
+    achieved_tf = FP64_FLOPS_PER_PT_STAGE * POINTS / (launch_ms * 1e-3) / 1e12
+    achieved_gbs = BYTES_PER_PT_STAGE * POINTS / (launch_ms * 1e-3) / 1e9
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "weights_dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WL.name, "nr": WL.nr, "ntheta": WL.nth, "a": WL.a, "s": WL.s,
+                   "m": WL.m, "wprec": "fp32", "rk": "SSP-RK(3,3)",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "fp64_weights": {"value": value64, "ms_per_step": ms64 / args.steps},
+        "mixed_speedup_vs_fp64_weights": value / value64,
+        "waveform_rel_l2_fp32_vs_fp64_weights": err,
+        "waveform_error_window": f"Psi(r*=100M, all theta) every 100 steps to t={t_err:.1f}M",
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS_MEASURED,
+                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS_MEASURED,
+                     "traffic": None, "pipe": "fp64",
+                     "peak_source": "measured FP64 FMA microbenchmark on GB300 "
+                                    "(profiles/fp64_pipe_microbenchmark.md); nominal 1.26",
+                     "kernel": "stage_kernel<fp32 weights>",
+                     "flops_per_point_stage": FP64_FLOPS_PER_PT_STAGE},
+        "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak,
+                         "bytes_per_point_stage": BYTES_PER_PT_STAGE},
+        "e2e": {"value": POINTS * 3 * e2e_steps * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+    }
+    v, n, el, cores = oracle_rate()
+    line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n} RK steps of the {WL.nr}x{WL.nth} workload "
+                                          f"(binary32 weights), {el:.1f} s"}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

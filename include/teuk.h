@@ -1,0 +1,193 @@
+/*
+ * teuk.h -- C ABI of the GB300 (sm_103a) mixed-precision WENO5 Teukolsky solver.
+ *
+ * The library advances one azimuthal m-mode of the Teukolsky master equation
+ * (arXiv 2010.04760, Eq. teuk0) on a 2+1-D (r*, theta) grid. Each Runge-Kutta
+ * stage evaluates the first-order system du/dt = -(M du/dr* + L u + A u)
+ * (Sec. 2.3, Eq. evln) with the WENO5 (Jiang-Shu) derivative in r*
+ * (Sec. 3.1.2), the nonlinear weights computed in a reduced precision
+ * (Sec. 3.1.3), fourth-order centred differences in theta (Sec. 3.1: "standard
+ * centered differencing"), and the SSP-RK(3,3) update (Sec. 3.2).
+ *
+ * Conventions shared by every call
+ *  - State vector u = {Psi_R, Psi_I, pi_R, pi_I} (Sec. 2.3). In memory it is
+ *    four planes, component-major: u[c][j][i], c = 0..3, j = theta row
+ *    0..ntheta-1, i = r* node 0..nr-1 (fastest). 4*ntheta*nr doubles.
+ *  - Grid: r*_i = rstar_min + i h, h = (rstar_max - rstar_min)/(nr - 1);
+ *    theta_j = (j + 1/2) pi / ntheta (cell centred, never on a pole).
+ *  - Time is Boyer-Lindquist t; the azimuth is the ingoing phi~ (Sec. 2.2),
+ *    Psi = exp(i m phi~) psi(t, r*, theta); pi = psi_t + b psi_*.
+ *  - Host pointers are read or written synchronously and stay owned by the
+ *    caller. Device pointers ("_dev") are caller-owned device memory on the
+ *    current CUDA device. Handles own their device memory.
+ *  - Every call returns a teuk_status; nothing throws across the ABI.
+ *    A failing call leaves its outputs unspecified and the handle usable
+ *    unless the status is TEUK_ERR_CUDA.
+ *  - "stream" arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).
+ */
+#ifndef TEUK_H
+#define TEUK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TEUK_OK = 0,
+    TEUK_ERR_ARG = 1,        /* invalid argument (message via teuk_last_error) */
+    TEUK_ERR_CUDA = 2,       /* a CUDA call failed                               */
+    TEUK_ERR_NONFINITE = 3,  /* the state holds a NaN or an infinity             */
+    TEUK_ERR_TIMEOUT = 4,    /* a device-side wait gave up                       */
+    TEUK_ERR_STATE = 5       /* call out of order (e.g. no state set yet)        */
+} teuk_status;
+
+/* Precision of the WENO smoothness indicators and nonlinear weights
+ * (Sec. 3.1.3). The derivative assembly, right-hand side and Runge-Kutta
+ * update are always binary64. */
+typedef enum {
+    TEUK_W_FP64 = 0,   /* Jiang-Shu weights in binary64 (the plain baseline)  */
+    TEUK_W_FP32 = 1,   /* weights in binary32                                 */
+    TEUK_W_FP16 = 2,   /* weights in binary16, indicators scaled into range   */
+    TEUK_W_BF16 = 3    /* weights in bfloat16, indicators scaled into range   */
+} teuk_wprec;
+
+/* Discretisation of the theta derivatives (Sec. 3.1). */
+typedef enum {
+    TEUK_THETA_CENTERED4 = 0   /* fourth-order centred, the paper's choice      */
+} teuk_theta_mode;
+
+/* Problem statement (Sec. 2.1-2.3, Sec. 4): grid, domain, black hole, mode.
+ * Valid ranges: nr >= 7, ntheta >= 5, rstar_max > rstar_min, M > 0,
+ * 0 <= |a| <= M, s in {-2..2}, |m| <= 64, eps in [1e-60, 1],
+ * dt > 0, or dt == 0 with cfl in (0, 1] (dt from the stability rule below). */
+typedef struct {
+    int nr, ntheta;                 /* grid nodes in r* and theta            */
+    double rstar_min, rstar_max;    /* r* domain in units of M               */
+    double M, a;                    /* mass and spin                         */
+    int s, m;                       /* spin weight, azimuthal number         */
+    double cfl;                     /* Courant factor when dt == 0           */
+    double dt;                      /* fixed time step, or 0                 */
+    double eps;                     /* WENO epsilon (Jiang-Shu use 1e-6)     */
+    int wprec;                      /* teuk_wprec                            */
+    int theta_mode;                 /* teuk_theta_mode                       */
+} teuk_params;
+
+typedef struct teuk_handle teuk_handle;
+typedef struct teuk_batch teuk_batch;
+
+/* ---- diagnostics ------------------------------------------------------- */
+
+/* Static description of a status code. Never NULL. */
+const char* teuk_status_str(teuk_status st);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* teuk_last_error(void);
+
+/* ---- host-side helpers ------------------------------------------------- */
+
+/* Validate p (see teuk_params). Returns TEUK_OK or TEUK_ERR_ARG. */
+teuk_status teuk_check_params(const teuk_params* p);
+
+/* Time step of the stability rule used when p->dt == 0:
+ *   dt = cfl / max_ij [ b/h + sqrt(kappa) ],
+ *   kappa = Ath (16/3)/dtheta^2 + |Bth| (3/2)/dtheta + |C|,
+ * a bound of the largest frequency of the r* upwind part (b/h, Sec. 3.2
+ * forward-Euler limit) plus the theta part of the second-order operator.
+ * If p->dt > 0 it is returned unchanged. */
+teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out);
+
+/* Number of doubles in the kernel coefficient array of p (11 planes of
+ * ntheta*nr). 0 if p is invalid. */
+size_t teuk_coeff_count(const teuk_params* p);
+
+/* Kernel coefficient array for time step dt, written to host memory
+ * coef_host[teuk_coeff_count(p)]. The planes are the first-order matrices
+ * M, A, L of Sec. 2.3 pre-multiplied by dt (and 1/(6h), 1/(12 dtheta^k) for
+ * the stencil normalisations), with the theta pole parity folded into the
+ * five theta-stencil planes. Built on the host in binary64; r(r*) from the
+ * tortoise relation of Sec. 2.2. */
+teuk_status teuk_build_coefficients(const teuk_params* p, double dt,
+                                    double* coef_host);
+
+/* ---- stateless device entry points (caller-owned device memory) --------- */
+
+/* One fused SSP-RK(3,3) stage (Sec. 3.2) on device arrays:
+ *   stage 1: u_out = u_prev + dt F(u_prev)
+ *   stage 2: u_out = 3/4 u_n + 1/4 (u_prev + dt F(u_prev))
+ *   stage 3: u_out = 1/3 u_n + 2/3 (u_prev + dt F(u_prev))
+ *   stage 0: u_out = dt F(u_prev)   (the operator alone, for checks)
+ * F is the right-hand side of Eq. evln with the WENO5 r* derivative.
+ * dt must be the step coef_dev was built for (teuk_build_coefficients).
+ * coef_dev: teuk_coeff_count(p) doubles. u_n (read for stages 2, 3; may be
+ * NULL otherwise), u_prev, u_out: 4*ntheta*nr doubles. u_out must not alias
+ * u_prev; it may alias u_n (each node reads u_n only at itself).
+ * Asynchronous on stream. Returns TEUK_ERR_ARG for bad p, dt, stage or
+ * pointers, TEUK_ERR_CUDA if the launch fails. */
+teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_dev,
+                           const double* u_n, const double* u_prev,
+                           double* u_out, int stage, void* stream);
+
+/* nsteps full SSP-RK(3,3) steps (Sec. 3.2) in place on u_dev, using caller
+ * scratch work_dev of 8*ntheta*nr doubles (the two intermediate stages).
+ * dt, coef_dev as for teuk_stage_dev. Asynchronous on stream; u_dev holds
+ * the state after the last step. work_dev must not overlap u_dev. */
+teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_dev,
+                          double* u_dev, double* work_dev, int64_t nsteps,
+                          void* stream);
+
+/* ---- handle API (library-owned device memory) --------------------------- */
+
+/* Allocate the state, stage buffers and coefficient array on the current
+ * device and build the coefficients (teuk_stable_dt when p->dt == 0).
+ * stream: the CUDA stream every later call of this handle runs on.
+ * The state starts at zero, t = 0. */
+teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out);
+
+/* Free everything the handle owns. NULL is accepted. */
+teuk_status teuk_destroy(teuk_handle* h);
+
+/* Parameters and the time step actually used. */
+teuk_status teuk_get_info(const teuk_handle* h, teuk_params* p_out,
+                          double* dt_out, double* t_out);
+
+/* Initial data from host arrays (Sec. 4: the field and its momentum):
+ * psi, pi: [ntheta][nr] complex values as interleaved (re, im) doubles,
+ * 2*ntheta*nr each. Sets t = 0. Synchronous. */
+teuk_status teuk_set_initial(teuk_handle* h, const double* psi,
+                             const double* pi);
+
+/* Checkpoint: copy the planar state u[4][ntheta][nr] and time t in or out
+ * (host memory, synchronous). Restoring a saved state and stepping gives
+ * bitwise the same result as never having stopped. */
+teuk_status teuk_set_state(teuk_handle* h, const double* u_host, double t);
+teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out);
+
+/* Advance nsteps SSP-RK(3,3) steps (3 fused stage launches each, replayed
+ * from a captured CUDA graph). Asynchronous on the handle's stream. */
+teuk_status teuk_step(teuk_handle* h, int64_t nsteps);
+
+/* Observation (Sec. 4): wave[2*ntheta] = Psi (re, im) along theta at the r*
+ * node nearest rstar_ext; horizon[6*ntheta] = for each theta row, Psi, pi
+ * and dPsi/dr* (one-sided, second order) at the innermost node i = 0, each
+ * as (re, im). Either output may be NULL. t_out (may be NULL) = current t.
+ * Synchronises the handle's stream. Returns TEUK_ERR_NONFINITE if a gathered
+ * value is not finite. */
+teuk_status teuk_observe(teuk_handle* h, double rstar_ext, double* wave,
+                         double* horizon, double* t_out);
+
+/* Device reduction over the whole state; TEUK_ERR_NONFINITE if any entry is
+ * NaN or infinite. Synchronises the handle's stream. */
+teuk_status teuk_check_finite(teuk_handle* h);
+
+/* Device pointer of the state planes (valid until teuk_destroy). */
+teuk_status teuk_state_dev(teuk_handle* h, double** u_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEUK_H */

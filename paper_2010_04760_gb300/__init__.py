@@ -1,0 +1,258 @@
+"""GB300 (sm_103a) mixed-precision WENO5 Teukolsky solver (arXiv 2010.04760).
+
+Thin Python binding of the C ABI declared in ``include/teuk.h``: every
+function here has the C function's name and only marshals arguments; all
+arithmetic runs in the CUDA library ``libteuk.so`` built next to this file by
+``paper_2010_04760_gb300.build``. There is no CPU fallback: if the library is
+missing, every call raises.
+
+Device arrays are passed as CUDA ``torch`` tensors (float64, contiguous) or as
+raw integer device pointers; host arrays as numpy float64 arrays. Streams are
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or None.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libteuk.so")
+
+TEUK_OK, TEUK_ERR_ARG, TEUK_ERR_CUDA, TEUK_ERR_NONFINITE, TEUK_ERR_TIMEOUT, TEUK_ERR_STATE = range(6)
+TEUK_W_FP64, TEUK_W_FP32, TEUK_W_FP16, TEUK_W_BF16 = range(4)
+TEUK_THETA_CENTERED4 = 0
+WPREC = {"fp64": TEUK_W_FP64, "fp32": TEUK_W_FP32, "fp16": TEUK_W_FP16, "bf16": TEUK_W_BF16}
+COEF_PLANES = 11
+
+
+class TeukError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class teuk_params(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("ntheta", ctypes.c_int),
+                ("rstar_min", ctypes.c_double), ("rstar_max", ctypes.c_double),
+                ("M", ctypes.c_double), ("a", ctypes.c_double),
+                ("s", ctypes.c_int), ("m", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
+                ("eps", ctypes.c_double), ("wprec", ctypes.c_int),
+                ("theta_mode", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2010_04760_gb300.build.build() "
+                               "(needs nvcc); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, I, I64, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        PP = ctypes.POINTER(teuk_params)
+        sig = {
+            "teuk_status_str": (ctypes.c_char_p, [I]),
+            "teuk_last_error": (ctypes.c_char_p, []),
+            "teuk_check_params": (I, [PP]),
+            "teuk_stable_dt": (I, [PP, P]),
+            "teuk_coeff_count": (S, [PP]),
+            "teuk_build_coefficients": (I, [PP, D, P]),
+            "teuk_stage_dev": (I, [PP, D, P, P, P, P, I, P]),
+            "teuk_step_dev": (I, [PP, D, P, P, P, I64, P]),
+            "teuk_create": (I, [PP, P, P]),
+            "teuk_destroy": (I, [P]),
+            "teuk_get_info": (I, [P, PP, P, P]),
+            "teuk_set_initial": (I, [P, P, P]),
+            "teuk_set_state": (I, [P, P, D]),
+            "teuk_get_state": (I, [P, P, P]),
+            "teuk_step": (I, [P, I64]),
+            "teuk_observe": (I, [P, D, P, P, P]),
+            "teuk_check_finite": (I, [P]),
+            "teuk_state_dev": (I, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names of the functions include/teuk.h declares (parsed from the header)."""
+    import re
+    hdr = os.path.join(_HERE, "..", "include", "teuk.h")
+    with open(hdr) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|teuk_status|size_t)\s+(teuk_\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def _check(st):
+    if st != TEUK_OK:
+        msg = lib().teuk_last_error().decode() or lib().teuk_status_str(st).decode()
+        raise TeukError(st, msg)
+
+
+def _dptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda or x.dtype.__str__() != "torch.float64" or not x.is_contiguous():
+            raise ValueError("device arrays must be contiguous CUDA float64 tensors")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError("expected a CUDA tensor or an integer device pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _host(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(nr, ntheta, rstar_min=-100.0, rstar_max=300.0, M=1.0, a=0.0, s=0, m=0,
+                cfl=0.5, dt=0.0, eps=1e-6, wprec="fp64", theta_mode=TEUK_THETA_CENTERED4):
+    w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    return teuk_params(nr, ntheta, rstar_min, rstar_max, M, a, s, m, cfl, dt, eps, w, theta_mode)
+
+
+def params_from_workload(wl, **over):
+    kw = dict(nr=wl.nr, ntheta=wl.nth, rstar_min=wl.rs_min, rstar_max=wl.rs_max, M=wl.M, a=wl.a,
+              s=wl.s, m=wl.m, cfl=wl.cfl, eps=wl.eps, wprec=wl.wprec)
+    kw.update(over)
+    return make_params(**kw)
+
+
+# ---- C-ABI functions (same names) ------------------------------------------
+
+def teuk_status_str(st):
+    return lib().teuk_status_str(st).decode()
+
+
+def teuk_last_error():
+    return lib().teuk_last_error().decode()
+
+
+def teuk_check_params(p):
+    return lib().teuk_check_params(ctypes.byref(p))
+
+
+def teuk_stable_dt(p):
+    out = ctypes.c_double()
+    _check(lib().teuk_stable_dt(ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+def teuk_coeff_count(p):
+    return lib().teuk_coeff_count(ctypes.byref(p))
+
+
+def teuk_build_coefficients(p, dt):
+    n = teuk_coeff_count(p)
+    if n == 0:
+        _check(lib().teuk_check_params(ctypes.byref(p)))
+    out = np.zeros((COEF_PLANES, p.ntheta, p.nr))
+    _check(lib().teuk_build_coefficients(ctypes.byref(p), dt, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def teuk_stage_dev(p, dt, coef_dev, u_n, u_prev, u_out, stage, stream=None):
+    _check(lib().teuk_stage_dev(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_n), _dptr(u_prev),
+                                _dptr(u_out), int(stage), _stream(stream)))
+
+
+def teuk_step_dev(p, dt, coef_dev, u_dev, work_dev, nsteps, stream=None):
+    _check(lib().teuk_step_dev(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_dev),
+                               _dptr(work_dev), int(nsteps), _stream(stream)))
+
+
+class Handle:
+    """Owner of a teuk_handle*; the methods are the handle calls of teuk.h."""
+
+    def __init__(self, ptr, p):
+        self.ptr = ptr
+        self.p = p
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.ptr:
+            lib().teuk_destroy(self.ptr)
+            self.ptr = None
+
+
+def teuk_create(p, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().teuk_create(ctypes.byref(p), _stream(stream), ctypes.byref(h)))
+    return Handle(h, p)
+
+
+def teuk_destroy(h):
+    h.close()
+
+
+def teuk_get_info(h):
+    p, dt, t = teuk_params(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().teuk_get_info(h.ptr, ctypes.byref(p), ctypes.byref(dt), ctypes.byref(t)))
+    return p, dt.value, t.value
+
+
+def teuk_set_initial(h, psi, pi):
+    """psi, pi: complex arrays [ntheta, nr]."""
+    ps = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
+    pc = np.ascontiguousarray(np.asarray(pi, dtype=np.complex128))
+    _check(lib().teuk_set_initial(h.ptr, ps.ctypes.data_as(ctypes.c_void_p),
+                                  pc.ctypes.data_as(ctypes.c_void_p)))
+
+
+def teuk_set_state(h, u, t=0.0):
+    arr, ptr = _host(u)
+    _check(lib().teuk_set_state(h.ptr, ptr, float(t)))
+
+
+def teuk_get_state(h, out=None):
+    if out is None:
+        out = np.empty((4, h.p.ntheta, h.p.nr))
+    t = ctypes.c_double()
+    _check(lib().teuk_get_state(h.ptr, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
+    return out, t.value
+
+
+def teuk_step(h, nsteps):
+    _check(lib().teuk_step(h.ptr, int(nsteps)))
+
+
+def teuk_observe(h, rstar_ext):
+    wave = np.empty((h.p.ntheta, 2))
+    hor = np.empty((h.p.ntheta, 6))
+    t = ctypes.c_double()
+    _check(lib().teuk_observe(h.ptr, float(rstar_ext), wave.ctypes.data_as(ctypes.c_void_p),
+                              hor.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
+    return wave, hor, t.value
+
+
+def teuk_check_finite(h):
+    return lib().teuk_check_finite(h.ptr)
+
+
+def teuk_state_dev(h):
+    ptr = ctypes.c_void_p()
+    _check(lib().teuk_state_dev(h.ptr, ctypes.byref(ptr)))
+    return ptr.value

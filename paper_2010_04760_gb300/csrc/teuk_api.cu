@@ -1,0 +1,284 @@
+// C ABI: stateless device entry points, the handle (library-owned memory,
+// CUDA-graph stepping), observation and the non-finite check.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "teuk_internal.h"
+
+namespace teuk {
+
+cudaError_t launch_stage(const teuk_params& p, const double* coef, const double* un,
+                         const double* up, double* out, int stage, double dt,
+                         cudaStream_t st);
+
+static teuk_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(TEUK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define TEUK_CUDA(call)                                         \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+// One SSP-RK(3,3) step: u -> w1 -> w2 -> u (Sec. 3.2).
+static cudaError_t launch_step(const teuk_params& p, const double* coef, double dt,
+                               double* u, double* w1, double* w2, cudaStream_t st) {
+    cudaError_t e = launch_stage(p, coef, nullptr, u, w1, 1, dt, st);
+    if (e == cudaSuccess) e = launch_stage(p, coef, u, w1, w2, 2, dt, st);
+    if (e == cudaSuccess) e = launch_stage(p, coef, u, w2, u, 3, dt, st);
+    return e;
+}
+
+// Sets *flag when any of n values is NaN or infinite.
+__global__ void nonfinite_kernel(const double* __restrict__ u, long long n, int* flag) {
+    int bad = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(u[k]);
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// obs[2j..] = Psi at (ie, j); obs[2 nth + 6j ..] = Psi, pi, dPsi/dr* at i = 0.
+__global__ void observe_kernel(const double* __restrict__ u, int nr, int nth, long long plane,
+                               int ie, double inv2h, double* obs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nth) return;
+    const long long row = (long long)j * nr;
+    obs[2 * j] = u[row + ie];
+    obs[2 * j + 1] = u[plane + row + ie];
+    double* hz = obs + 2 * nth + 6 * j;
+    for (int c = 0; c < 4; ++c) hz[c] = u[c * plane + row];
+    for (int c = 0; c < 2; ++c) {
+        const double* f = u + c * plane + row;
+        hz[4 + c] = (-3.0 * f[0] + 4.0 * f[1] - f[2]) * inv2h;
+    }
+}
+
+}  // namespace teuk
+
+using namespace teuk;
+
+struct teuk_handle {
+    teuk_params p;
+    double dt = 0.0, t = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double* u = nullptr;
+    double* w = nullptr;      // two stage buffers
+    double* coef = nullptr;
+    double* obs = nullptr;
+    int* flag = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int chunk = 0;
+    size_t plane() const { return (size_t)p.nr * p.ntheta; }
+};
+
+extern "C" {
+
+teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_dev,
+                           const double* u_n, const double* u_prev, double* u_out,
+                           int stage, void* stream) {
+    teuk_status st = teuk_check_params(p);
+    if (st != TEUK_OK) return st;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+    if (stage < 0 || stage > 3) return fail(TEUK_ERR_ARG, "stage must be 0..3");
+    if (!coef_dev || !u_prev || !u_out) return fail(TEUK_ERR_ARG, "NULL device pointer");
+    if (stage >= 2 && !u_n) return fail(TEUK_ERR_ARG, "u_n is NULL for stage 2/3");
+    if (u_out == u_prev) return fail(TEUK_ERR_ARG, "u_out aliases u_prev");
+    TEUK_CUDA(launch_stage(*p, coef_dev, u_n, u_prev, u_out, stage, dt, (cudaStream_t)stream));
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_dev,
+                          double* u_dev, double* work_dev, int64_t nsteps, void* stream) {
+    teuk_status st = teuk_check_params(p);
+    if (st != TEUK_OK) return st;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+    if (!coef_dev || !u_dev || !work_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
+    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+    const size_t n = 4 * (size_t)p->nr * p->ntheta;
+    if (work_dev < u_dev + n && u_dev < work_dev + 2 * n)
+        return fail(TEUK_ERR_ARG, "work_dev overlaps u_dev");
+    for (int64_t k = 0; k < nsteps; ++k)
+        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, work_dev, work_dev + n,
+                              (cudaStream_t)stream));
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_destroy(teuk_handle* h) {
+    if (!h) return TEUK_OK;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    cudaFree(h->u);
+    cudaFree(h->w);
+    cudaFree(h->coef);
+    cudaFree(h->obs);
+    cudaFree(h->flag);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return TEUK_OK;
+}
+
+teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
+    if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    teuk_status st = teuk_check_params(p);
+    if (st != TEUK_OK) return st;
+    teuk_handle* h = new teuk_handle();
+    h->p = *p;
+    st = teuk_stable_dt(p, &h->dt);
+    if (st != TEUK_OK) { delete h; return st; }
+    const size_t n = h->plane();
+    std::vector<double> coef((size_t)kCoefPlanes * n);
+    st = teuk_build_coefficients(p, h->dt, coef.data());
+    if (st != TEUK_OK) { delete h; return st; }
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        h->own_stream = (e == cudaSuccess);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->u, 4 * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->w, 8 * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->coef, coef.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->obs, 8 * (size_t)p->ntheta * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 4 * n * sizeof(double), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->coef, coef.data(), coef.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        teuk_destroy(h);
+        return cuda_fail(e, "teuk_create");
+    }
+    *out = h;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_get_info(const teuk_handle* h, teuk_params* p_out, double* dt_out,
+                          double* t_out) {
+    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+    if (p_out) *p_out = h->p;
+    if (dt_out) *dt_out = h->dt;
+    if (t_out) *t_out = h->t;
+    return TEUK_OK;
+}
+
+teuk_status teuk_set_state(teuk_handle* h, const double* u_host, double t) {
+    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+    TEUK_CUDA(cudaMemcpyAsync(h->u, u_host, 4 * h->plane() * sizeof(double),
+                              cudaMemcpyHostToDevice, h->stream));
+    TEUK_CUDA(cudaStreamSynchronize(h->stream));
+    h->t = t;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out) {
+    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+    TEUK_CUDA(cudaMemcpyAsync(u_host, h->u, 4 * h->plane() * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    TEUK_CUDA(cudaStreamSynchronize(h->stream));
+    if (t_out) *t_out = h->t;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_set_initial(teuk_handle* h, const double* psi, const double* pi) {
+    if (!h || !psi || !pi) return fail(TEUK_ERR_ARG, "NULL argument");
+    const size_t n = h->plane();
+    std::vector<double> u(4 * n);
+    for (size_t k = 0; k < n; ++k) {
+        u[k] = psi[2 * k];
+        u[n + k] = psi[2 * k + 1];
+        u[2 * n + k] = pi[2 * k];
+        u[3 * n + k] = pi[2 * k + 1];
+    }
+    return teuk_set_state(h, u.data(), 0.0);
+}
+
+teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
+    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+    const int kChunk = 16;
+    double* w1 = h->w;
+    double* w2 = h->w + 4 * h->plane();
+    if (nsteps >= kChunk && !h->exec) {
+        cudaGraph_t g = nullptr;
+        TEUK_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kChunk && e == cudaSuccess; ++k)
+            e = launch_step(h->p, h->coef, h->dt, h->u, w1, w2, h->stream);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { h->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+        h->chunk = kChunk;
+    }
+    int64_t left = nsteps;
+    while (h->exec && left >= h->chunk) {
+        TEUK_CUDA(cudaGraphLaunch(h->exec, h->stream));
+        left -= h->chunk;
+    }
+    for (; left > 0; --left)
+        TEUK_CUDA(launch_step(h->p, h->coef, h->dt, h->u, w1, w2, h->stream));
+    h->t += (double)nsteps * h->dt;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_observe(teuk_handle* h, double rstar_ext, double* wave, double* horizon,
+                         double* t_out) {
+    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+    if (!std::isfinite(rstar_ext)) return fail(TEUK_ERR_ARG, "rstar_ext not finite");
+    const int nr = h->p.nr, nth = h->p.ntheta;
+    const double hstep = (h->p.rstar_max - h->p.rstar_min) / (nr - 1);
+    long ie = std::lround((rstar_ext - h->p.rstar_min) / hstep);
+    ie = ie < 0 ? 0 : (ie > nr - 1 ? nr - 1 : ie);
+    observe_kernel<<<(nth + 127) / 128, 128, 0, h->stream>>>(
+        h->u, nr, nth, (long long)h->plane(), (int)ie, 0.5 / hstep, h->obs);
+    TEUK_CUDA(cudaGetLastError());
+    std::vector<double> o(8 * (size_t)nth);
+    TEUK_CUDA(cudaMemcpyAsync(o.data(), h->obs, o.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    TEUK_CUDA(cudaStreamSynchronize(h->stream));
+    for (double v : o)
+        if (!std::isfinite(v)) return fail(TEUK_ERR_NONFINITE, "observed value is not finite");
+    if (wave) std::memcpy(wave, o.data(), 2 * (size_t)nth * sizeof(double));
+    if (horizon) std::memcpy(horizon, o.data() + 2 * nth, 6 * (size_t)nth * sizeof(double));
+    if (t_out) *t_out = h->t;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_check_finite(teuk_handle* h) {
+    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+    TEUK_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    nonfinite_kernel<<<304, 256, 0, h->stream>>>(h->u, 4 * (long long)h->plane(), h->flag);
+    TEUK_CUDA(cudaGetLastError());
+    int flag = 0;
+    TEUK_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    TEUK_CUDA(cudaStreamSynchronize(h->stream));
+    if (flag) return fail(TEUK_ERR_NONFINITE, "state holds NaN or infinity");
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_state_dev(teuk_handle* h, double** u_dev) {
+    if (!h || !u_dev) return fail(TEUK_ERR_ARG, "NULL argument");
+    *u_dev = h->u;
+    return TEUK_OK;
+}
+
+}  // extern "C"

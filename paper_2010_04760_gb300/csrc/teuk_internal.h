@@ -1,0 +1,29 @@
+// Internal declarations shared by the host (.cpp) and device (.cu) parts of
+// the library. Not part of the public ABI.
+#pragma once
+#include <string>
+#include "../../include/teuk.h"
+
+namespace teuk {
+
+// Number of coefficient planes the stage kernel reads per grid node.
+constexpr int kCoefPlanes = 11;
+// Plane order (all pre-multiplied by dt):
+//   0 cb   = b/(6h)          1 cKr = Re K/(6h)     2 cKi = Im K/(6h)
+//   3 cBr  = Re Bt           4 cBi = Im Bt         5 cCi = Im C
+//   6..10  theta stencil weights on Psi rows j-2, j-1, j, j+1, j+2
+//          (Ath and Bth centred differences, Re C on the centre, pole parity
+//          folded in).
+enum CoefPlane { kCb = 0, kCKr, kCKi, kCBr, kCBi, kCCi, kWm2, kWm1, kW0, kWp1, kWp2 };
+
+teuk_status fail(teuk_status st, const std::string& msg);
+void clear_error();
+
+// r(r*) and the continuum coefficients at one node, real arithmetic.
+struct PointCoef {
+    double b, Kr, Ki, Btr, Bti, Cr, Ci, Ath, Bth;
+};
+double r_of_rstar(double rstar, double M, double a, double* x_out);
+PointCoef point_coefficients(double rstar, double theta, const teuk_params& p);
+
+}  // namespace teuk

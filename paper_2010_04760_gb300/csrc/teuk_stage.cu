@@ -1,0 +1,382 @@
+// Fused WENO5 / Teukolsky right-hand side / SSP-RK(3,3) stage kernel for
+// sm_103a, and the stateless device entry points of the C ABI.
+//
+// One warp owns a segment of SEG consecutive r* nodes of one theta row. It
+//   1. forms the binary64 first differences d_k = f_{k+1} - f_k of the four
+//      components over the segment plus its halo (r* ghosts copy the edge
+//      value, Sec. 3.1 reading),
+//   2. forms s_k = d_{k-1} - 2 d_k + d_{k+1},
+//   3. at every interface computes the nonlinear weights (Sec. 3.1.2) in the
+//      requested precision (Sec. 3.1.3) and the binary64 flux term
+//         F = x1 + 2 x2 - 2 w0 s(x0,x1,x2) - w2 s(x1,x2,x3),
+//      which equals 6 (fhat_{i+1/2} - f_i) for the positive-direction flux
+//      with x = (d_{i-2}, d_{i-1}, d_i, d_{i+1}); the negative-direction flux
+//      is its mirror image (x = d_{i+2}, d_{i+1}, d_i, d_{i-1}, G = -F),
+//   4. at every node forms 6 h D = 6 d + F_{i+1/2} - F_{i-1/2}, the theta
+//      stencil, the right-hand side -(M du + L u + A u) (Sec. 2.3) and the
+//      SSP-RK(3,3) combination (Sec. 3.2), and stores the new stage.
+// Every binary64 quantity is formed once per node (no recomputation inside a
+// segment); the weights run on the FP32 pipes. The only binary64 operations
+// are the differences, the weighted flux combination, the right-hand side and
+// the Runge-Kutta update.
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "teuk_internal.h"
+
+namespace teuk {
+
+constexpr int SEG = 64;          // r* nodes per warp
+constexpr int WARPS = 4;         // theta rows per CTA (one per warp)
+constexpr int ND = SEG + 5;      // first differences d_k, k in [i0-3, i0+SEG+1]
+constexpr int NS = SEG + 3;      // s_k, k in [i0-2, i0+SEG]
+constexpr int NF = SEG + 1;      // interfaces i+1/2, i in [i0-1, i0+SEG-1]
+constexpr int NW = ND + NS + NF; // doubles per component per warp
+
+struct StageArgs {
+    const double* coef;   // kCoefPlanes planes of nth*nr
+    const double* un;     // u^n (stages 2, 3)
+    const double* up;     // u^{(s-1)}, the operator's argument
+    double* out;          // may alias un (read only at the same node)
+    int nr, nth;
+    long long plane;
+    double dt;            // step (the Psi rows need dt * pi)
+    double alpha, beta;   // u_out = alpha u^n + beta (u_prev + dt F)
+    double eps4;          // 4 eps (binary64 weights)
+    double eps;           // eps (reduced weights)
+};
+
+// ---------------------------------------------------------------------------
+// Exact bit-level helpers (integer pipes only).
+// ---------------------------------------------------------------------------
+
+// 2^q as a binary32, q in [-149, 127].
+__device__ __forceinline__ float pow2f(int q) {
+    return q >= -126 ? __int_as_float((q + 127) << 23) : __int_as_float(1 << (q + 149));
+}
+
+// |x| 2^-e rounded to P significant bits (ties to even), with the subnormal
+// spacing of a format whose smallest normal exponent is EMIN; returned as the
+// binary32 holding that value exactly (requires |x| 2^-e < 2^128).
+template <int P, int EMIN>
+__device__ __forceinline__ float round_scaled(double x, int e) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (bits >> 63) != 0;
+    const int E = (int)((bits >> 52) & 0x7ff);
+    unsigned long long m = bits & 0xfffffffffffffULL;
+    int ex;
+    if (E == 0) {
+        if (m == 0) return neg ? -0.0f : 0.0f;
+        ex = -1074;
+    } else {
+        m |= (1ULL << 52);
+        ex = E - 1075;
+    }
+    const int L = 64 - __clzll((long long)m);
+    const int lead = ex - e + L - 1;             // floor(log2(|x| 2^-e))
+    const int leff = lead < EMIN ? EMIN : lead;
+    const int q = leff - (P - 1);                // unit of the last place
+    const int sh = q - (ex - e);
+    unsigned long long n;
+    if (sh <= 0) {
+        n = m << (-sh);
+    } else if (sh >= 64) {
+        n = 0;
+    } else {
+        n = m >> sh;
+        const unsigned long long rem = m & ((1ULL << sh) - 1);
+        const unsigned long long half = 1ULL << (sh - 1);
+        if (rem > half || (rem == half && (n & 1ULL))) n += 1;
+    }
+    if (n == 0) return neg ? -0.0f : 0.0f;
+    const float v = __fmul_rn(__ull2float_rn(n), pow2f(q < -149 ? -149 : q));
+    return neg ? -v : v;
+}
+
+// binary32 -> binary64, exact, on the integer pipes (finite input).
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned E = (u >> 23) & 0xffu;
+    const unsigned mnt = u & 0x7fffffu;
+    if (E == 0) {
+        if (mnt == 0) return __hiloint2double((int)sign, 0);
+        const int p = 31 - __clz((int)mnt);                      // 0..22
+        const unsigned long long frac =
+            ((unsigned long long)(mnt ^ (1u << p))) << (52 - p);
+        const unsigned long long b = ((unsigned long long)sign << 32) |
+                                     ((unsigned long long)(p - 149 + 1023) << 52) | frac;
+        return __longlong_as_double((long long)b);
+    }
+    return __hiloint2double((int)(sign | ((E + 896u) << 20) | (mnt >> 3)), (int)(mnt << 29));
+}
+
+// ---------------------------------------------------------------------------
+// Weight formats. rw() rounds a binary32 value to the format; a binary32
+// operation followed by rw() is the correctly rounded operation of the
+// format (24 >= 2p + 2 for p = 11 and p = 8).
+// ---------------------------------------------------------------------------
+template <int W> struct Fmt;
+template <> struct Fmt<TEUK_W_FP32> {
+    static constexpr int P = 24, EMIN = -126, LOG2TINY = -126, LOG2HUGE = 100;
+    __device__ static float rw(float x) { return x; }
+};
+template <> struct Fmt<TEUK_W_FP16> {
+    static constexpr int P = 11, EMIN = -14, LOG2TINY = -14, LOG2HUGE = 15;
+    __device__ static float rw(float x) { return __half2float(__float2half_rn(x)); }
+};
+template <> struct Fmt<TEUK_W_BF16> {
+    static constexpr int P = 8, EMIN = -126, LOG2TINY = -126, LOG2HUGE = 100;
+    __device__ static float rw(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+};
+
+// floor(log2 max_k |x_k|) from the bit patterns (0 if all are zero).
+__device__ __forceinline__ int max_exponent(double x0, double x1, double x2, double x3) {
+    const unsigned long long k = 0x7fffffffffffffffULL;
+    unsigned long long a = (unsigned long long)__double_as_longlong(x0) & k;
+    a = max(a, (unsigned long long)__double_as_longlong(x1) & k);
+    a = max(a, (unsigned long long)__double_as_longlong(x2) & k);
+    a = max(a, (unsigned long long)__double_as_longlong(x3) & k);
+    const int E = (int)(a >> 52);
+    if (E > 0) return E - 1023;
+    if (a == 0) return 0;
+    return (63 - __clzll((long long)a)) - 1074;
+}
+
+// Reduced-precision Jiang-Shu weights omega_0, omega_2 (Sec. 3.1.2-3.1.3) of
+// the stencil with first differences x0..x3 (positive-direction order).
+// Smoothness indicators in first differences:
+//   IS0 = 13/12 (x1-x0)^2 + 1/4 (3x1-x0)^2
+//   IS1 = 13/12 (x2-x1)^2 + 1/4 (x1+x2)^2
+//   IS2 = 13/12 (x3-x2)^2 + 1/4 (3x2-x3)^2
+// The differences are scaled by 2^-e (e = floor(log2 max|x|)) before rounding
+// to the format, epsilon by 2^-2e (clamped to [tiny, huge]), and alpha_k is
+// normalised by the smallest eps + IS: alpha_k = d_k (t_min/t_k)^2. The
+// operation sequence is fixed (no contraction) so that every rounding is
+// determined.
+template <int W>
+__device__ __forceinline__ void reduced_weights(double x0, double x1, double x2, double x3,
+                                                double eps, float& w0, float& w2) {
+    using F = Fmt<W>;
+    const int e = max_exponent(x0, x1, x2, x3);
+    const float y0 = round_scaled<F::P, F::EMIN>(x0, e);
+    const float y1 = round_scaled<F::P, F::EMIN>(x1, e);
+    const float y2 = round_scaled<F::P, F::EMIN>(x2, e);
+    const float y3 = round_scaled<F::P, F::EMIN>(x3, e);
+    // eps 2^-2e, clamped, rounded to the format
+    float eh;
+    {
+        const unsigned long long eb = (unsigned long long)__double_as_longlong(eps);
+        const int Ee = (int)((eb >> 52) & 0x7ff) - 1023;     // eps is a normal number
+        const bool pow2 = (eb & 0xfffffffffffffULL) == 0;
+        const int lead = Ee - 2 * e;
+        if (lead < F::LOG2TINY) eh = pow2f(F::LOG2TINY);
+        else if (lead > F::LOG2HUGE || (lead == F::LOG2HUGE && !pow2)) eh = pow2f(F::LOG2HUGE);
+        else eh = round_scaled<F::P, F::EMIN>(eps, 2 * e);
+    }
+    const float c13 = F::rw((float)(13.0 / 12.0));
+    const float d0 = F::rw(0.1f), d1 = F::rw(0.6f), d2 = F::rw(0.3f);
+    float a, b, IS0, IS1, IS2;
+    a = F::rw(__fsub_rn(y1, y0));
+    b = F::rw(__fsub_rn(F::rw(__fmul_rn(3.0f, y1)), y0));
+    IS0 = F::rw(__fadd_rn(F::rw(__fmul_rn(c13, F::rw(__fmul_rn(a, a)))),
+                          F::rw(__fmul_rn(0.25f, F::rw(__fmul_rn(b, b))))));
+    a = F::rw(__fsub_rn(y2, y1));
+    b = F::rw(__fadd_rn(y1, y2));
+    IS1 = F::rw(__fadd_rn(F::rw(__fmul_rn(c13, F::rw(__fmul_rn(a, a)))),
+                          F::rw(__fmul_rn(0.25f, F::rw(__fmul_rn(b, b))))));
+    a = F::rw(__fsub_rn(y3, y2));
+    b = F::rw(__fsub_rn(F::rw(__fmul_rn(3.0f, y2)), y3));
+    IS2 = F::rw(__fadd_rn(F::rw(__fmul_rn(c13, F::rw(__fmul_rn(a, a)))),
+                          F::rw(__fmul_rn(0.25f, F::rw(__fmul_rn(b, b))))));
+    const float t0 = F::rw(__fadd_rn(eh, IS0));
+    const float t1 = F::rw(__fadd_rn(eh, IS1));
+    const float t2 = F::rw(__fadd_rn(eh, IS2));
+    const float tm = fminf(t0, fminf(t1, t2));
+    const float r0 = F::rw(__fdiv_rn(tm, t0));
+    const float r1 = F::rw(__fdiv_rn(tm, t1));
+    const float r2 = F::rw(__fdiv_rn(tm, t2));
+    const float a0 = F::rw(__fmul_rn(d0, F::rw(__fmul_rn(r0, r0))));
+    const float a1 = F::rw(__fmul_rn(d1, F::rw(__fmul_rn(r1, r1))));
+    const float a2 = F::rw(__fmul_rn(d2, F::rw(__fmul_rn(r2, r2))));
+    const float sum = F::rw(__fadd_rn(F::rw(__fadd_rn(a0, a1)), a2));
+    w0 = F::rw(__fdiv_rn(a0, sum));
+    w2 = F::rw(__fdiv_rn(a2, sum));
+}
+
+// 6 (fhat_{i+1/2} - f_i) for first differences x0..x3 (positive-direction
+// order) and s1 = x0 - 2x1 + x2, s2 = x1 - 2x2 + x3:
+//   q0 - q1 = -s1/3, q2 - q1 = -s2/6, q1 - f_i = (x1 + 2 x2)/6.
+template <int W>
+__device__ __forceinline__ double flux6(double x0, double x1, double x2, double x3,
+                                        double s1, double s2, const StageArgs& A) {
+    const double base = fma(2.0, x2, x1);
+    if constexpr (W == TEUK_W_FP64) {
+        // 4 (eps + IS_k) = (13/3) a^2 + b^2 + 4 eps; omega from one reciprocal:
+        //   omega_0 = d0 t1^2 t2^2 / S, omega_2 = d2 t0^2 t1^2 / S,
+        //   S = d0 t1^2 t2^2 + d1 t0^2 t2^2 + d2 t0^2 t1^2.
+        const double c133 = 13.0 / 3.0;
+        const double a0 = x1 - x0, b0 = fma(3.0, x1, -x0);
+        const double a1 = x2 - x1, b1 = x1 + x2;
+        const double a2 = x3 - x2, b2 = fma(3.0, x2, -x3);
+        const double t0 = fma(c133 * a0, a0, fma(b0, b0, A.eps4));
+        const double t1 = fma(c133 * a1, a1, fma(b1, b1, A.eps4));
+        const double t2 = fma(c133 * a2, a2, fma(b2, b2, A.eps4));
+        const double q0 = t0 * t0, q1 = t1 * t1, q2 = t2 * t2;
+        const double p12 = q1 * q2, p02 = q0 * q2, p01 = q0 * q1;
+        const double n0 = 0.1 * p12, n2 = 0.3 * p01;
+        const double S = fma(0.6, p02, n0 + n2);
+        const double rS = __drcp_rn(S);
+        const double w0 = n0 * rS, w2 = n2 * rS;
+        return fma(-w2, s2, fma(-2.0 * w0, s1, base));
+    } else {
+        float w0, w2;
+        reduced_weights<W>(x0, x1, x2, x3, A.eps, w0, w2);
+        const double m2w0 = f2d_exact(-2.0f * w0);   // exact
+        const double mw2 = f2d_exact(-w2);
+        return fma(mw2, s2, fma(m2w0, s1, base));
+    }
+}
+
+template <int W, int STAGE>
+__global__ void __launch_bounds__(WARPS * 32) stage_kernel(const StageArgs A) {
+    __shared__ double sm[WARPS][4 * NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.y * WARPS + warp;
+    if (j >= A.nth) return;
+    const int nr = A.nr;
+    const int i0 = blockIdx.x * SEG;
+    const long long row = (long long)j * nr;
+    double* sw = sm[warp];
+#define DL(c, k) sw[(c) * NW + (k)]
+#define SD(c, k) sw[(c) * NW + ND + (k)]
+#define FL(c, k) sw[(c) * NW + ND + NS + (k)]
+
+    // 1. first differences d_k, k = i0-3 .. i0+SEG+1 (edge ghosts: d = 0)
+    for (int idx = lane; idx < 4 * ND; idx += 32) {
+        const int c = idx / ND, k = idx - c * ND;
+        const int g = i0 - 3 + k;
+        const double* f = A.up + c * A.plane + row;
+        const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
+        DL(c, k) = __ldg(f + ib) - __ldg(f + ia);
+    }
+    __syncwarp();
+    // 2. s_k = d_{k-1} - 2 d_k + d_{k+1}, k = i0-2 .. i0+SEG
+    for (int idx = lane; idx < 4 * NS; idx += 32) {
+        const int c = idx / NS, k = idx - c * NS;
+        SD(c, k) = fma(-2.0, DL(c, k + 1), DL(c, k) + DL(c, k + 2));
+    }
+    __syncwarp();
+    // 3. interface flux terms, i + 1/2 for i = i0-1 .. i0+SEG-1
+    for (int idx = lane; idx < 4 * NF; idx += 32) {
+        const int c = idx / NF, k = idx - c * NF;
+        double F;
+        if (c < 2) {   // Psi: positive-direction flux, x = d_{i-2..i+1}
+            F = flux6<W>(DL(c, k), DL(c, k + 1), DL(c, k + 2), DL(c, k + 3),
+                         SD(c, k), SD(c, k + 1), A);
+        } else {       // pi: negative-direction flux, mirrored stencil
+            F = -flux6<W>(DL(c, k + 4), DL(c, k + 3), DL(c, k + 2), DL(c, k + 1),
+                          SD(c, k + 2), SD(c, k + 1), A);
+        }
+        FL(c, k) = F;
+    }
+    __syncwarp();
+    // 4. nodes i = i0 .. i0+SEG-1
+    const double* cf = A.coef + row;
+    const long long P = A.plane;
+    for (int p = lane; p < SEG; p += 32) {
+        const int i = i0 + p;
+        if (i >= nr) break;
+        // 6 h D for each component
+        const double D0 = fma(6.0, DL(0, p + 2), FL(0, p + 1)) - FL(0, p);
+        const double D1 = fma(6.0, DL(1, p + 2), FL(1, p + 1)) - FL(1, p);
+        const double D2 = fma(6.0, DL(2, p + 3), FL(2, p + 1)) - FL(2, p);
+        const double D3 = fma(6.0, DL(3, p + 3), FL(3, p + 1)) - FL(3, p);
+        const long long q = row + i;
+        const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
+        const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
+        const double cb = __ldg(cf + kCb * P + i), cKr = __ldg(cf + kCKr * P + i);
+        const double cKi = __ldg(cf + kCKi * P + i), cBr = __ldg(cf + kCBr * P + i);
+        const double cBi = __ldg(cf + kCBi * P + i), cCi = __ldg(cf + kCCi * P + i);
+        double acc0, acc1, acc2, acc3;
+        if (STAGE == 0) {
+            acc0 = A.dt * pir; acc1 = A.dt * pii; acc2 = 0.0; acc3 = 0.0;
+        } else {
+            acc0 = fma(A.dt, pir, psr); acc1 = fma(A.dt, pii, psi); acc2 = pir; acc3 = pii;
+        }
+        // Psi rows: dt (pi - b D_Psi)
+        acc0 = fma(-cb, D0, acc0);
+        acc1 = fma(-cb, D1, acc1);
+        // pi rows: dt (b D_pi + K D_Psi + Bt pi + i Im(C) Psi + theta terms)
+        acc2 = fma(cb, D2, acc2);
+        acc2 = fma(cKr, D0, acc2);
+        acc2 = fma(-cKi, D1, acc2);
+        acc2 = fma(cBr, pir, acc2);
+        acc2 = fma(-cBi, pii, acc2);
+        acc2 = fma(-cCi, psi, acc2);
+        acc3 = fma(cb, D3, acc3);
+        acc3 = fma(cKi, D0, acc3);
+        acc3 = fma(cKr, D1, acc3);
+        acc3 = fma(cBi, pir, acc3);
+        acc3 = fma(cBr, pii, acc3);
+        acc3 = fma(cCi, psr, acc3);
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            const int jj = min(max(j + k, 0), A.nth - 1);   // weight is 0 off-grid
+            const double w = __ldg(cf + (kW0 + k) * P + i);
+            const long long qq = (long long)jj * nr + i;
+            acc2 = fma(w, __ldg(A.up + qq), acc2);
+            acc3 = fma(w, __ldg(A.up + P + qq), acc3);
+        }
+        if (STAGE >= 2) {
+            acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
+            acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
+            acc2 = fma(A.beta, acc2, A.alpha * A.un[2 * P + q]);
+            acc3 = fma(A.beta, acc3, A.alpha * A.un[3 * P + q]);
+        }
+        A.out[q] = acc0;
+        A.out[P + q] = acc1;
+        A.out[2 * P + q] = acc2;
+        A.out[3 * P + q] = acc3;
+    }
+#undef DL
+#undef SD
+#undef FL
+}
+
+template <int W>
+static cudaError_t launch_stage_w(const StageArgs& A, int stage, cudaStream_t st) {
+    dim3 grid((A.nr + SEG - 1) / SEG, (A.nth + WARPS - 1) / WARPS);
+    dim3 block(WARPS * 32);
+    switch (stage) {
+    case 0: stage_kernel<W, 0><<<grid, block, 0, st>>>(A); break;
+    case 1: stage_kernel<W, 1><<<grid, block, 0, st>>>(A); break;
+    case 2: stage_kernel<W, 2><<<grid, block, 0, st>>>(A); break;
+    default: stage_kernel<W, 3><<<grid, block, 0, st>>>(A); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage(const teuk_params& p, const double* coef, const double* un,
+                         const double* up, double* out, int stage, double dt,
+                         cudaStream_t st) {
+    StageArgs A;
+    A.coef = coef; A.un = un; A.up = up; A.out = out;
+    A.nr = p.nr; A.nth = p.ntheta;
+    A.plane = (long long)p.nr * p.ntheta;
+    A.dt = dt;
+    A.alpha = stage == 2 ? 0.75 : (stage == 3 ? 1.0 / 3.0 : 0.0);
+    A.beta = stage == 2 ? 0.25 : (stage == 3 ? 2.0 / 3.0 : 1.0);
+    A.eps = p.eps;
+    A.eps4 = 4.0 * p.eps;
+    switch (p.wprec) {
+    case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, st);
+    case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, st);
+    case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, st);
+    default: return launch_stage_w<TEUK_W_BF16>(A, stage, st);
+    }
+}
+
+}  // namespace teuk

@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element, on
+seeded inputs, through the C ABI. Weights of every precision are computed on
+both sides with the same rounding sequence, so the tolerance is binary64
+round-off of the (differently arranged) stencil arithmetic for every weight
+format: |gpu - oracle| <= 1e-12 max|oracle| per component."""
+import numpy as np
+import pytest
+
+import oracle as o
+import paper_2010_04760_gb300 as T
+from paper_2010_04760_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    T.lib()
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def oracle_dt(g, co):
+    """Test-side time step: 0.5 / max(b/h + sqrt(theta frequencies))."""
+    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth = co
+    h = (g.rs_max - g.rs_min) / (g.nr - 1)
+    dth = np.pi / g.nth
+    kap = Ath * (16 / 3) / dth ** 2 + np.abs(Bth) * 1.5 / dth + np.hypot(Cr, Ci)
+    return 0.5 / np.max(b / h + np.sqrt(kap))
+
+
+def multiscale_state(nr, nth, seed, smooth):
+    u = I.random_state(nr, nth, seed, smooth=smooth)
+    rng = np.random.default_rng(seed + 100)
+    scale = 10.0 ** rng.uniform(-40, 6, size=(1, nth, 1))
+    u = u * scale
+    u[:, :, : nr // 8] *= 1e-200          # deep tail region (weights set by eps)
+    return u
+
+
+def term_scale(u, dt, g, co):
+    """Size of the individual terms of dt F(u): dt max(b) max|u| / h. Round-off
+    of the stencil sums is relative to this, not to the (possibly much
+    smaller) result."""
+    h = (g.rs_max - g.rs_min) / (g.nr - 1)
+    return dt * np.max(co[0]) * np.max(np.abs(u)) / h
+
+
+def compare(got, exp_, tol=TOL, what="", terms=0.0):
+    for c in range(4):
+        sc = max(np.max(np.abs(exp_[c])), terms)
+        err = np.max(np.abs(got[c] - exp_[c]))
+        assert err <= tol * sc + 1e-300, f"{what} component {c}: err {err:.3e} scale {sc:.3e}"
+
+
+SHAPES = [(7, 5), (64, 8), (100, 13), (257, 33), (1000, 17)]
+PHYS = [(0.999, -2, 2), (0.0, 0, 0), (1.0, 0, 1), (0.5, -1, 0)]
+
+
+@pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("phys", PHYS)
+def test_operator_parity(wprec, shape, phys):
+    nr, nth = shape
+    a, s, m = phys
+    rs0, rs1 = -40.0, 120.0
+    seed = nr * 7 + nth
+    for smooth in (True, False):
+        u = multiscale_state(nr, nth, seed, smooth)
+        g = o.grid(nr, nth, rs0, rs1, 1.0, a, s, m, 1e-6, wprec)
+        F = o.rhs(g, o.coefficients(g), u)
+        p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m, wprec=wprec)
+        coef = dev(T.teuk_build_coefficients(p, 1.0))
+        ud = dev(u)
+        out = torch.empty_like(ud)
+        T.teuk_stage_dev(p, 1.0, coef, None, ud, out, 0)
+        compare(host(out), F, what=f"{wprec} {shape} {phys} smooth={smooth}")
+
+
+@pytest.mark.parametrize("wprec", ["fp64", "fp32"])
+def test_rk_stages_parity(wprec):
+    nr, nth, a, s, m = 300, 20, 0.9, -2, 1
+    rs0, rs1 = -50.0, 150.0
+    g = o.grid(nr, nth, rs0, rs1, 1.0, a, s, m, 1e-6, wprec)
+    co = o.coefficients(g)
+    dt = oracle_dt(g, co)
+    un = I.random_state(nr, nth, 1)
+    up = I.random_state(nr, nth, 2)
+    p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m, wprec=wprec)
+    coef = dev(T.teuk_build_coefficients(p, dt))
+    Fp = o.rhs(g, co, up)
+    exp_ = {1: up + dt * Fp, 2: 0.75 * un + 0.25 * (up + dt * Fp),
+            3: un / 3.0 + 2.0 / 3.0 * (up + dt * Fp)}
+    for stage in (1, 2, 3):
+        out = torch.empty(4, nth, nr, dtype=torch.float64, device="cuda")
+        T.teuk_stage_dev(p, dt, coef, dev(un), dev(up), out, stage)
+        compare(host(out), exp_[stage], tol=1e-13, what=f"stage {stage}")
+    # stage 3 in place on u_n (the library's own step layout)
+    una = dev(un)
+    T.teuk_stage_dev(p, dt, coef, una, dev(up), una, 3)
+    compare(host(una), exp_[3], tol=1e-13, what="stage 3 in place")
+
+
+def run_both(wl, wprec, nsteps, u0=None):
+    """nsteps of SSP-RK(3,3) on the GPU (stateless step) and in the oracle."""
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec)
+    co = o.coefficients(g)
+    dt = oracle_dt(g, co)
+    u0 = I.initial_data(wl) if u0 is None else u0
+    p = T.params_from_workload(wl, wprec=wprec)
+    coef = dev(T.teuk_build_coefficients(p, dt))
+    ud = dev(u0)
+    work = torch.empty(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    T.teuk_step_dev(p, dt, coef, ud, work, nsteps)
+    return host(ud), o.rk3_step(g, co, dt, u0, nsteps), term_scale(u0, dt, g, co)
+
+
+@pytest.mark.parametrize("wprec", ["fp64", "fp32"])
+def test_full_size_kerr_gravitational(wprec):
+    """2048 x 128, s=-2, m=2, a=0.999 (the benchmark workload), 3 steps,
+    every node compared."""
+    got, exp_, ts = run_both(I.KERR_GRAV, wprec, 3)
+    compare(got, exp_, what=f"kerr {wprec}", terms=ts)
+
+
+@pytest.mark.parametrize("wprec", ["fp16", "bf16"])
+def test_full_size_extremal_scalar(wprec):
+    """8192 x 256, s=0, m=0, a=M, one step, every node compared."""
+    got, exp_, ts = run_both(I.EXTREMAL_SCALAR, wprec, 1)
+    compare(got, exp_, what=f"extremal {wprec}", terms=ts)
+
+
+def test_tail_workload_full_size_one_stage():
+    """16384 x 512 (tail workload, binary32 weights): one stage, every node."""
+    wl = I.TAIL_SCALAR
+    u0 = I.initial_data(wl)
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, "fp32")
+    p = T.params_from_workload(wl)
+    dt = 0.05
+    coef = dev(T.teuk_build_coefficients(p, dt))
+    ud = dev(u0)
+    out = torch.empty_like(ud)
+    T.teuk_stage_dev(p, dt, coef, None, ud, out, 1)
+    got = host(out)
+    del out, ud, coef
+    co = o.coefficients(g)
+    exp_ = u0 + dt * o.rhs(g, co, u0)
+    compare(got, exp_, what="tail workload", terms=term_scale(u0, dt, g, co))
+
+
+def test_waveform_parity_schwarzschild_500_steps():
+    """256 x 32, s=m=a=0, binary64 weights, 500 steps: waveform at r*=100 over
+    the whole run, relative L2 <= 1e-12."""
+    wl = I.SCHW_SCALAR
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, 1.0, 0.0, 0, 0, 1e-6, "fp64")
+    co = o.coefficients(g)
+    dt = oracle_dt(g, co)
+    p = T.params_from_workload(wl, dt=dt)
+    h = T.teuk_create(p)
+    u = I.initial_data(wl)
+    T.teuk_set_state(h, u, 0.0)
+    wg, wo = [], []
+    uo = u.copy()
+    for _ in range(10):
+        T.teuk_step(h, 50)
+        wave, hor, t = T.teuk_observe(h, 100.0)
+        wg.append(wave.copy())
+        uo = o.rk3_step(g, co, dt, uo, 50)
+        w2, _ = o.observe(g, uo, 100.0)
+        wo.append(w2)
+    wg, wo = np.array(wg), np.array(wo)
+    rel = np.linalg.norm(wg - wo) / np.linalg.norm(wo)
+    assert rel <= 1e-12, rel
+    assert abs(t - 500 * dt) < 1e-9
+
+
+def test_handle_checkpoint_and_graph_bitwise():
+    wl = I.KERR_GRAV.with_(nr=300, nth=24)
+    p = T.params_from_workload(wl, wprec="fp32")
+    h1 = T.teuk_create(p)
+    u0 = I.initial_data(wl)
+    T.teuk_set_state(h1, u0, 0.0)
+    T.teuk_step(h1, 37)                                   # graph (2 x 16) + 5 direct
+    ref, t1 = T.teuk_get_state(h1)
+    h2 = T.teuk_create(p)
+    T.teuk_set_state(h2, u0, 0.0)
+    T.teuk_step(h2, 20)
+    mid, tm = T.teuk_get_state(h2)
+    h3 = T.teuk_create(p)
+    T.teuk_set_state(h3, mid, tm)
+    T.teuk_step(h3, 17)
+    res, t3 = T.teuk_get_state(h3)
+    np.testing.assert_array_equal(res, ref)
+    assert abs(t3 - t1) < 1e-12
+    # stateless stepping with caller scratch gives the same bits
+    _, dt, _ = T.teuk_get_info(h1)
+    coef = dev(T.teuk_build_coefficients(p, dt))
+    ud = dev(u0)
+    work = torch.empty(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    T.teuk_step_dev(p, dt, coef, ud, work, 37)
+    np.testing.assert_array_equal(host(ud), ref)
+
+
+def test_set_initial_and_observe():
+    wl = I.KERR_GRAV.with_(nr=200, nth=16)
+    p = T.params_from_workload(wl)
+    h = T.teuk_create(p)
+    u = I.initial_data(wl)
+    T.teuk_set_initial(h, u[0] + 1j * u[1], u[2] + 1j * u[3])
+    wave, hor, t = T.teuk_observe(h, 30.0)
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, 1.0, wl.a, wl.s, wl.m)
+    w2, h2 = o.observe(g, u, 30.0)
+    np.testing.assert_array_equal(wave, w2)
+    np.testing.assert_allclose(hor, h2, rtol=1e-15, atol=0)
+    assert t == 0.0
+
+
+def test_nonfinite_state_is_reported():
+    wl = I.SCHW_SCALAR
+    h = T.teuk_create(T.params_from_workload(wl))
+    u = I.initial_data(wl)
+    T.teuk_set_state(h, u)
+    assert T.teuk_check_finite(h) == T.TEUK_OK
+    u[2, 5, 17] = np.nan                                  # host-made failure
+    T.teuk_set_state(h, u)
+    assert T.teuk_check_finite(h) == T.TEUK_ERR_NONFINITE
+    u[2, 5, 17] = 0.0
+    u[0, 3, 0] = np.inf
+    T.teuk_set_state(h, u)
+    with pytest.raises(T.TeukError) as ei:
+        T.teuk_observe(h, 0.0)
+    assert ei.value.status == T.TEUK_ERR_NONFINITE
+
+
+def test_device_entry_points_reject_bad_arguments():
+    p = T.make_params(64, 8)
+    coef = dev(T.teuk_build_coefficients(p, 0.1))
+    u = torch.zeros(4, 8, 64, dtype=torch.float64, device="cuda")
+    out = torch.zeros_like(u)
+    for stage, un, dt in [(4, None, 0.1), (2, None, 0.1), (1, None, 0.0)]:
+        with pytest.raises(T.TeukError) as ei:
+            T.teuk_stage_dev(p, dt, coef, un, u, out, stage)
+        assert ei.value.status == T.TEUK_ERR_ARG
+    with pytest.raises(T.TeukError):
+        T.teuk_stage_dev(p, 0.1, coef, None, u, u, 1)       # out aliases u_prev

@@ -1,0 +1,95 @@
+"""Host-side tests of the C ABI (no GPU): the library loads and exports every
+symbol include/teuk.h declares, arguments are validated, and the host
+coefficient generator (independent code) agrees with the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as o
+import paper_2010_04760_gb300 as T
+from paper_2010_04760_gb300 import build as B
+from paper_2010_04760_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def test_library_exports_every_declared_symbol():
+    names = T.declared_symbols()
+    assert len(names) >= 18
+    L = T.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings():
+    for st in range(6):
+        assert T.teuk_status_str(st)
+
+
+@pytest.mark.parametrize("field,value", [("nr", 6), ("ntheta", 4), ("a", 1.5), ("M", 0.0),
+                                         ("s", 3), ("eps", 0.0), ("wprec", 7), ("cfl", 0.0),
+                                         ("rstar_max", -200.0), ("dt", -1.0), ("theta_mode", 9),
+                                         ("m", 65)])
+def test_check_params_rejects(field, value):
+    p = T.make_params(64, 16)
+    setattr(p, field, value)
+    assert T.teuk_check_params(p) == T.TEUK_ERR_ARG
+    assert T.teuk_last_error()
+
+
+def test_check_params_accepts_workloads():
+    for wl in [I.SCHW_SCALAR, I.KERR_GRAV, I.EXTREMAL_SCALAR, I.TAIL_SCALAR]:
+        assert T.teuk_check_params(T.params_from_workload(wl)) == T.TEUK_OK
+
+
+def test_stable_dt_rule():
+    p = T.make_params(256, 32, a=0.0, s=0, m=0, cfl=0.5)
+    dt = T.teuk_stable_dt(p)
+    h = 400.0 / 255
+    assert 0.0 < dt < 0.5 * h        # the upwind part alone allows cfl * h / b
+    p.dt = 0.01
+    assert T.teuk_stable_dt(p) == 0.01
+
+
+@pytest.mark.parametrize("a,s,m", [(0.0, 0, 0), (0.999, -2, 2), (1.0, 0, 0), (0.4, -1, 1),
+                                   (0.7, -2, 3)])
+def test_coefficients_agree_with_oracle(a, s, m):
+    nr, nth, rs0, rs1, dt = 40, 12, -60.0, 120.0, 0.07
+    p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m)
+    got = T.teuk_build_coefficients(p, dt)
+    co = o.coefficients(o.grid(nr, nth, rs0, rs1, 1.0, a, s, m))
+    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth = co
+    h = (rs1 - rs0) / (nr - 1)
+    dth = np.pi / nth
+    tol = dict(rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(got[0], dt * b / (6 * h), **tol)
+    np.testing.assert_allclose(got[1], dt * Kr / (6 * h), **tol)
+    np.testing.assert_allclose(got[2], dt * Ki / (6 * h), **tol)
+    np.testing.assert_allclose(got[3], dt * Br, **tol)
+    np.testing.assert_allclose(got[4], dt * Bi, **tol)
+    np.testing.assert_allclose(got[5], dt * Ci, **tol)
+    # theta planes applied to a pole-parity-respecting field reproduce
+    # Ath Psi_thth + Bth Psi_th + Re C Psi from the oracle's ghost-cell operator
+    rng = np.random.default_rng(0)
+    psi = rng.standard_normal((nth, nr))
+    sig = 1.0 if (m + s) % 2 == 0 else -1.0
+    acc = np.zeros((nth, nr))
+    for k in range(-2, 3):
+        rows = np.clip(np.arange(nth) + k, 0, nth - 1)
+        acc += got[8 + k] * psi[rows]
+    ext = np.concatenate([sig * psi[1::-1], psi, sig * psi[:-3:-1]])   # rows -2..nth+1
+    nb = [ext[2 + k:2 + k + nth] for k in range(-2, 3)]
+    th1 = (nb[0] - 8 * nb[1] + 8 * nb[3] - nb[4]) / (12 * dth)
+    th2 = (-nb[0] + 16 * nb[1] - 30 * nb[2] + 16 * nb[3] - nb[4]) / (12 * dth ** 2)
+    exp_ = dt * (Ath * th2 + Bth * th1 + Cr * psi)
+    np.testing.assert_allclose(acc, exp_, rtol=1e-8, atol=1e-10 * np.max(np.abs(exp_)))
+
+
+def test_build_coefficients_rejects_bad_dt():
+    p = T.make_params(64, 16)
+    with pytest.raises(T.TeukError):
+        T.teuk_build_coefficients(p, 0.0)
