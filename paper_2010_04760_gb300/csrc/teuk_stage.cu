@@ -23,13 +23,30 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <cstring>
 
 #include "teuk_internal.h"
 
 namespace teuk {
 
-constexpr int SEG = 64;          // r* nodes per warp
-constexpr int WARPS = 4;         // theta rows per CTA (one per warp)
+#ifndef TEUK_SEG
+#define TEUK_SEG 64
+#endif
+#ifndef TEUK_WARPS
+#define TEUK_WARPS 4
+#endif
+#ifndef TEUK_MINB
+#define TEUK_MINB 8                // resident CTAs per SM the register budget targets
+#endif
+#define TEUK_BOUNDS __launch_bounds__(TEUK_WARPS * 32, TEUK_MINB)
+#ifndef TEUK_ILP
+#define TEUK_ILP 1                 // interfaces per lane and iteration in the flux phase
+#endif
+#ifndef TEUK_SPLIT
+#define TEUK_SPLIT 0               // theta terms in a separate partial sum
+#endif
+constexpr int SEG = TEUK_SEG;    // r* nodes per warp
+constexpr int WARPS = TEUK_WARPS;  // theta rows per CTA (one per warp)
 constexpr int ND = SEG + 5;      // first differences d_k, k in [i0-3, i0+SEG+1]
 constexpr int NS = SEG + 3;      // s_k, k in [i0-2, i0+SEG]
 constexpr int NF = SEG + 1;      // interfaces i+1/2, i in [i0-1, i0+SEG-1]
@@ -45,7 +62,10 @@ struct StageArgs {
     double dt;            // step (the Psi rows need dt * pi)
     double alpha, beta;   // u_out = alpha u^n + beta (u_prev + dt F)
     double eps4;          // 4 eps (binary64 weights)
-    double eps;           // eps (reduced weights)
+    int eps_exp;          // floor(log2 eps)
+    int eps_pow2;         // eps is a power of two
+    unsigned eps_mant;    // binary32 bits of eps 2^-eps_exp rounded to the
+                          // weight format (a value in [1, 2])
 };
 
 // ---------------------------------------------------------------------------
@@ -62,7 +82,9 @@ __device__ __forceinline__ float pow2f(int q) {
 // binary32 holding that value exactly (requires |x| 2^-e < 2^128).
 template <int P, int EMIN>
 __device__ __forceinline__ float round_scaled(double x, int e) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    // bit pattern from the 32-bit halves (see max_exponent)
+    const unsigned long long bits = ((unsigned long long)(unsigned)__double2hiint(x) << 32) |
+                                    (unsigned)__double2loint(x);
     const bool neg = (bits >> 63) != 0;
     const int E = (int)((bits >> 52) & 0x7ff);
     unsigned long long m = bits & 0xfffffffffffffULL;
@@ -91,8 +113,38 @@ __device__ __forceinline__ float round_scaled(double x, int e) {
         if (rem > half || (rem == half && (n & 1ULL))) n += 1;
     }
     if (n == 0) return neg ? -0.0f : 0.0f;
-    const float v = __fmul_rn(__ull2float_rn(n), pow2f(q < -149 ? -149 : q));
+    // n <= 2^P <= 2^24: a 32-bit conversion is exact (a 64-bit one would run
+    // on the FP64 pipe)
+    const float v = __fmul_rn(__uint2float_rn((unsigned)n), pow2f(q < -149 ? -149 : q));
     return neg ? -v : v;
+}
+
+// Same result as round_scaled for a normal x whose scaled value is normal in
+// the format, with 32-bit integer operations only; other inputs take the
+// general path.
+template <int P, int EMIN>
+__device__ __forceinline__ float round_scaled_fast(double x, int e) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int E = (int)((hi >> 20) & 0x7ffu);
+    const int t = E - 1023 - e;                      // floor(log2(|x| 2^-e))
+    if (E == 0 || t < EMIN) return round_scaled<P, EMIN>(x, e);
+    constexpr int D = 53 - P;                        // dropped significand bits
+    unsigned kept, rup;
+    if constexpr (D < 32) {
+        kept = ((hi & 0xfffffu) << (32 - D)) | (lo >> D);
+        const unsigned dropped = lo & ((1u << D) - 1u);
+        const unsigned half = 1u << (D - 1);
+        rup = (dropped > half || (dropped == half && (kept & 1u))) ? 1u : 0u;
+    } else {
+        constexpr int DH = D - 32;
+        kept = (hi & 0xfffffu) >> DH;
+        const unsigned dh = hi & ((1u << DH) - 1u);
+        const unsigned half = 1u << (DH - 1);
+        rup = (dh > half || (dh == half && (lo != 0u || (kept & 1u)))) ? 1u : 0u;
+    }
+    // a carry out of the significand increments the exponent field
+    const unsigned mag = ((unsigned)(t + 127) << 23) + ((kept + rup) << (24 - P));
+    return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
 // binary32 -> binary64, exact, on the integer pipes (finite input).
@@ -106,9 +158,8 @@ __device__ __forceinline__ double f2d_exact(float f) {
         const int p = 31 - __clz((int)mnt);                      // 0..22
         const unsigned long long frac =
             ((unsigned long long)(mnt ^ (1u << p))) << (52 - p);
-        const unsigned long long b = ((unsigned long long)sign << 32) |
-                                     ((unsigned long long)(p - 149 + 1023) << 52) | frac;
-        return __longlong_as_double((long long)b);
+        const unsigned long long b = ((unsigned long long)(p - 149 + 1023) << 52) | frac;
+        return __hiloint2double((int)(sign | (unsigned)(b >> 32)), (int)(unsigned)b);
     }
     return __hiloint2double((int)(sign | ((E + 896u) << 20) | (mnt >> 3)), (int)(mnt << 29));
 }
@@ -134,13 +185,24 @@ template <> struct Fmt<TEUK_W_BF16> {
 
 // floor(log2 max_k |x_k|) from the bit patterns (0 if all are zero).
 __device__ __forceinline__ int max_exponent(double x0, double x1, double x2, double x3) {
-    const unsigned long long k = 0x7fffffffffffffffULL;
-    unsigned long long a = (unsigned long long)__double_as_longlong(x0) & k;
-    a = max(a, (unsigned long long)__double_as_longlong(x1) & k);
-    a = max(a, (unsigned long long)__double_as_longlong(x2) & k);
-    a = max(a, (unsigned long long)__double_as_longlong(x3) & k);
-    const int E = (int)(a >> 52);
-    if (E > 0) return E - 1023;
+    unsigned ex = (unsigned)__double2hiint(x0) & 0x7ff00000u;
+    ex = max(ex, (unsigned)__double2hiint(x1) & 0x7ff00000u);
+    ex = max(ex, (unsigned)__double2hiint(x2) & 0x7ff00000u);
+    ex = max(ex, (unsigned)__double2hiint(x3) & 0x7ff00000u);
+    if (ex != 0u) return (int)(ex >> 20) - 1023;
+    // all zero or subnormal: the largest significand decides. The significand
+    // is assembled from the 32-bit halves (masking a reinterpreted double's
+    // sign bit would be turned into an absolute-value instruction on the
+    // FP64 pipe).
+    unsigned long long a = 0;
+    const double xs[4] = {x0, x1, x2, x3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned long long mk =
+            ((unsigned long long)((unsigned)__double2hiint(xs[k]) & 0xfffffu) << 32) |
+            (unsigned)__double2loint(xs[k]);
+        a = max(a, mk);
+    }
     if (a == 0) return 0;
     return (63 - __clzll((long long)a)) - 1074;
 }
@@ -158,23 +220,23 @@ __device__ __forceinline__ int max_exponent(double x0, double x1, double x2, dou
 // determined.
 template <int W>
 __device__ __forceinline__ void reduced_weights(double x0, double x1, double x2, double x3,
-                                                double eps, float& w0, float& w2) {
+                                                const StageArgs& A, float& w0, float& w2) {
     using F = Fmt<W>;
     const int e = max_exponent(x0, x1, x2, x3);
-    const float y0 = round_scaled<F::P, F::EMIN>(x0, e);
-    const float y1 = round_scaled<F::P, F::EMIN>(x1, e);
-    const float y2 = round_scaled<F::P, F::EMIN>(x2, e);
-    const float y3 = round_scaled<F::P, F::EMIN>(x3, e);
-    // eps 2^-2e, clamped, rounded to the format
+    const float y0 = round_scaled_fast<F::P, F::EMIN>(x0, e);
+    const float y1 = round_scaled_fast<F::P, F::EMIN>(x1, e);
+    const float y2 = round_scaled_fast<F::P, F::EMIN>(x2, e);
+    const float y3 = round_scaled_fast<F::P, F::EMIN>(x3, e);
+    // eps 2^-2e clamped to [tiny, huge], rounded to the format. Inside the
+    // clamp range the value is normal in the format, so rounding it is
+    // rounding eps's significand (precomputed) and shifting the exponent.
     float eh;
     {
-        const unsigned long long eb = (unsigned long long)__double_as_longlong(eps);
-        const int Ee = (int)((eb >> 52) & 0x7ff) - 1023;     // eps is a normal number
-        const bool pow2 = (eb & 0xfffffffffffffULL) == 0;
-        const int lead = Ee - 2 * e;
+        const int lead = A.eps_exp - 2 * e;
         if (lead < F::LOG2TINY) eh = pow2f(F::LOG2TINY);
-        else if (lead > F::LOG2HUGE || (lead == F::LOG2HUGE && !pow2)) eh = pow2f(F::LOG2HUGE);
-        else eh = round_scaled<F::P, F::EMIN>(eps, 2 * e);
+        else if (lead > F::LOG2HUGE || (lead == F::LOG2HUGE && !A.eps_pow2))
+            eh = pow2f(F::LOG2HUGE);
+        else eh = __uint_as_float(A.eps_mant + ((unsigned)lead << 23));
     }
     const float c13 = F::rw((float)(13.0 / 12.0));
     const float d0 = F::rw(0.1f), d1 = F::rw(0.6f), d2 = F::rw(0.3f);
@@ -208,11 +270,14 @@ __device__ __forceinline__ void reduced_weights(double x0, double x1, double x2,
 
 // 6 (fhat_{i+1/2} - f_i) for first differences x0..x3 (positive-direction
 // order) and s1 = x0 - 2x1 + x2, s2 = x1 - 2x2 + x3:
-//   q0 - q1 = -s1/3, q2 - q1 = -s2/6, q1 - f_i = (x1 + 2 x2)/6.
-template <int W>
+//   q0 - q1 = -s1/3, q2 - q1 = -s2/6, q1 - f_i = (x1 + 2 x2)/6,
+//   6 (fhat - f_i) = x1 + 2 x2 - 2 omega_0 s1 - omega_2 s2.
+// NEG returns the negated value (the negative-direction flux term), with the
+// sign folded into the multiply-adds.
+template <int W, bool NEG>
 __device__ __forceinline__ double flux6(double x0, double x1, double x2, double x3,
                                         double s1, double s2, const StageArgs& A) {
-    const double base = fma(2.0, x2, x1);
+    const double base = NEG ? fma(-2.0, x2, -x1) : fma(2.0, x2, x1);
     if constexpr (W == TEUK_W_FP64) {
         // 4 (eps + IS_k) = (13/3) a^2 + b^2 + 4 eps; omega from one reciprocal:
         //   omega_0 = d0 t1^2 t2^2 / S, omega_2 = d2 t0^2 t1^2 / S,
@@ -226,22 +291,111 @@ __device__ __forceinline__ double flux6(double x0, double x1, double x2, double 
         const double t2 = fma(c133 * a2, a2, fma(b2, b2, A.eps4));
         const double q0 = t0 * t0, q1 = t1 * t1, q2 = t2 * t2;
         const double p12 = q1 * q2, p02 = q0 * q2, p01 = q0 * q1;
-        const double n0 = 0.1 * p12, n2 = 0.3 * p01;
-        const double S = fma(0.6, p02, n0 + n2);
+        const double S = fma(0.1, p12, fma(0.6, p02, 0.3 * p01));
         const double rS = __drcp_rn(S);
-        const double w0 = n0 * rS, w2 = n2 * rS;
-        return fma(-w2, s2, fma(-2.0 * w0, s1, base));
+        const double c1 = (NEG ? 0.2 : -0.2) * p12 * rS;   // -+ 2 omega_0
+        const double c2 = (NEG ? 0.3 : -0.3) * p01 * rS;   // -+ omega_2
+        return fma(c2, s2, fma(c1, s1, base));
     } else {
         float w0, w2;
-        reduced_weights<W>(x0, x1, x2, x3, A.eps, w0, w2);
-        const double m2w0 = f2d_exact(-2.0f * w0);   // exact
-        const double mw2 = f2d_exact(-w2);
-        return fma(mw2, s2, fma(m2w0, s1, base));
+        reduced_weights<W>(x0, x1, x2, x3, A, w0, w2);
+        const double c1 = f2d_exact(NEG ? 2.0f * w0 : -2.0f * w0);   // exact
+        const double c2 = f2d_exact(NEG ? w2 : -w2);
+        return fma(c2, s2, fma(c1, s1, base));
     }
 }
 
+// Flux term of interface number idx (component idx / NF) of a warp's segment;
+// sw is the warp's shared-memory block (first differences, then s, then flux).
+// Psi components take the positive-direction flux, x = d_{i-2..i+1}; pi
+// components the negative-direction one, whose stencil is the mirror image
+// (x = d_{i+2..i-1}) and whose flux term is the negated positive form. The
+// stencil is chosen by integer index and the sign applied to the bit pattern,
+// so that no binary64 instruction is spent on either.
+template <int W>
+__device__ __forceinline__ double interface_flux(const double* sw, int idx, const StageArgs& A) {
+    const int c = idx / NF, k = idx - c * NF;
+    const double* dl = sw + c * NW;
+    const double* sd = dl + ND;
+    const bool neg = c >= 2;
+    const double F = flux6<W, false>(dl[neg ? k + 4 : k], dl[neg ? k + 3 : k + 1], dl[k + 2],
+                                     dl[neg ? k + 1 : k + 3], sd[neg ? k + 2 : k], sd[k + 1], A);
+    const int hi = __double2hiint(F) ^ (neg ? (int)0x80000000 : 0);
+    return __hiloint2double(hi, __double2loint(F));
+}
+
+// Right-hand side and Runge-Kutta combination at node i0 + p of row j
+// (Sec. 2.3, Sec. 3.2). sw holds the segment's first differences and flux
+// terms. Loads use a clamped node index; the caller stores only real nodes.
+template <int STAGE>
+__device__ __forceinline__ void node_update(const StageArgs& A, const double* sw, int j,
+                                            int i0, int p, double out[4]) {
+    const int nr = A.nr;
+    const int i = min(i0 + p, nr - 1);
+    const long long P = A.plane;
+    const long long q = (long long)j * nr + i;
+    const double* cf = A.coef + q;
+    // 6 h D for each component
+    const double D0 = fma(6.0, sw[0 * NW + p + 2], sw[0 * NW + ND + NS + p + 1]) - sw[0 * NW + ND + NS + p];
+    const double D1 = fma(6.0, sw[1 * NW + p + 2], sw[1 * NW + ND + NS + p + 1]) - sw[1 * NW + ND + NS + p];
+    const double D2 = fma(6.0, sw[2 * NW + p + 3], sw[2 * NW + ND + NS + p + 1]) - sw[2 * NW + ND + NS + p];
+    const double D3 = fma(6.0, sw[3 * NW + p + 3], sw[3 * NW + ND + NS + p + 1]) - sw[3 * NW + ND + NS + p];
+    const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
+    const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
+    const double cb = __ldg(cf + kCb * P), cKr = __ldg(cf + kCKr * P);
+    const double cKi = __ldg(cf + kCKi * P), cBr = __ldg(cf + kCBr * P);
+    const double cBi = __ldg(cf + kCBi * P), cCi = __ldg(cf + kCCi * P);
+    double acc0, acc1, acc2, acc3;
+    if (STAGE == 0) {
+        acc0 = A.dt * pir; acc1 = A.dt * pii; acc2 = 0.0; acc3 = 0.0;
+    } else {
+        acc0 = fma(A.dt, pir, psr); acc1 = fma(A.dt, pii, psi); acc2 = pir; acc3 = pii;
+    }
+    // Psi rows: dt (pi - b D_Psi)
+    acc0 = fma(-cb, D0, acc0);
+    acc1 = fma(-cb, D1, acc1);
+    // pi rows: dt (b D_pi + K D_Psi + Bt pi + i Im(C) Psi + theta terms)
+    acc2 = fma(cb, D2, acc2);
+    acc2 = fma(cKr, D0, acc2);
+    acc2 = fma(-cKi, D1, acc2);
+    acc2 = fma(cBr, pir, acc2);
+    acc2 = fma(-cBi, pii, acc2);
+    acc2 = fma(-cCi, psi, acc2);
+    acc3 = fma(cb, D3, acc3);
+    acc3 = fma(cKi, D0, acc3);
+    acc3 = fma(cKr, D1, acc3);
+    acc3 = fma(cBi, pir, acc3);
+    acc3 = fma(cBr, pii, acc3);
+    acc3 = fma(cCi, psr, acc3);
+#if TEUK_SPLIT
+    double th2 = 0.0, th3 = 0.0;
+#else
+    double& th2 = acc2;
+    double& th3 = acc3;
+#endif
+#pragma unroll
+    for (int k = -2; k <= 2; ++k) {
+        const int jj = min(max(j + k, 0), A.nth - 1);   // weight is 0 off-grid
+        const double w = __ldg(cf + (kW0 + k) * P);
+        const long long qq = (long long)jj * nr + i;
+        th2 = fma(w, __ldg(A.up + qq), th2);
+        th3 = fma(w, __ldg(A.up + P + qq), th3);
+    }
+#if TEUK_SPLIT
+    acc2 += th2;
+    acc3 += th3;
+#endif
+    if (STAGE >= 2) {
+        acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
+        acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
+        acc2 = fma(A.beta, acc2, A.alpha * A.un[2 * P + q]);
+        acc3 = fma(A.beta, acc3, A.alpha * A.un[3 * P + q]);
+    }
+    out[0] = acc0; out[1] = acc1; out[2] = acc2; out[3] = acc3;
+}
+
 template <int W, int STAGE>
-__global__ void __launch_bounds__(WARPS * 32) stage_kernel(const StageArgs A) {
+__global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     __shared__ double sm[WARPS][4 * NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
@@ -269,81 +423,69 @@ __global__ void __launch_bounds__(WARPS * 32) stage_kernel(const StageArgs A) {
         SD(c, k) = fma(-2.0, DL(c, k + 1), DL(c, k) + DL(c, k + 2));
     }
     __syncwarp();
-    // 3. interface flux terms, i + 1/2 for i = i0-1 .. i0+SEG-1
+    // 3. interface flux terms, i + 1/2 for i = i0-1 .. i0+SEG-1; two
+    //    independent interfaces per lane and iteration for instruction-level
+    //    parallelism
+#if TEUK_ILP == 1
     for (int idx = lane; idx < 4 * NF; idx += 32) {
-        const int c = idx / NF, k = idx - c * NF;
-        double F;
-        if (c < 2) {   // Psi: positive-direction flux, x = d_{i-2..i+1}
-            F = flux6<W>(DL(c, k), DL(c, k + 1), DL(c, k + 2), DL(c, k + 3),
-                         SD(c, k), SD(c, k + 1), A);
-        } else {       // pi: negative-direction flux, mirrored stencil
-            F = -flux6<W>(DL(c, k + 4), DL(c, k + 3), DL(c, k + 2), DL(c, k + 1),
-                          SD(c, k + 2), SD(c, k + 1), A);
-        }
-        FL(c, k) = F;
+        const int c = idx / NF;
+        FL(c, idx - c * NF) = interface_flux<W>(sw, idx, A);
     }
+#else
+    for (int idx = lane; idx < 4 * NF; idx += 64) {
+        const int idx2 = idx + 32;
+        const double Fa = interface_flux<W>(sw, idx, A);
+        double Fb = 0.0;
+        if (idx2 < 4 * NF) Fb = interface_flux<W>(sw, idx2, A);
+        {
+            const int c = idx / NF;
+            FL(c, idx - c * NF) = Fa;
+        }
+        if (idx2 < 4 * NF) {
+            const int c = idx2 / NF;
+            FL(c, idx2 - c * NF) = Fb;
+        }
+    }
+#endif
     __syncwarp();
-    // 4. nodes i = i0 .. i0+SEG-1
-    const double* cf = A.coef + row;
-    const long long P = A.plane;
-    for (int p = lane; p < SEG; p += 32) {
-        const int i = i0 + p;
-        if (i >= nr) break;
-        // 6 h D for each component
-        const double D0 = fma(6.0, DL(0, p + 2), FL(0, p + 1)) - FL(0, p);
-        const double D1 = fma(6.0, DL(1, p + 2), FL(1, p + 1)) - FL(1, p);
-        const double D2 = fma(6.0, DL(2, p + 3), FL(2, p + 1)) - FL(2, p);
-        const double D3 = fma(6.0, DL(3, p + 3), FL(3, p + 1)) - FL(3, p);
-        const long long q = row + i;
-        const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
-        const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
-        const double cb = __ldg(cf + kCb * P + i), cKr = __ldg(cf + kCKr * P + i);
-        const double cKi = __ldg(cf + kCKi * P + i), cBr = __ldg(cf + kCBr * P + i);
-        const double cBi = __ldg(cf + kCBi * P + i), cCi = __ldg(cf + kCCi * P + i);
-        double acc0, acc1, acc2, acc3;
-        if (STAGE == 0) {
-            acc0 = A.dt * pir; acc1 = A.dt * pii; acc2 = 0.0; acc3 = 0.0;
-        } else {
-            acc0 = fma(A.dt, pir, psr); acc1 = fma(A.dt, pii, psi); acc2 = pir; acc3 = pii;
+    // 4. nodes i = i0 .. i0+SEG-1 (two per lane and iteration, computed
+    //    side by side; the second node's loads use a clamped index and its
+    //    store is predicated)
+    for (int p = lane; p < SEG; p += 64) {
+        double ua[4], ub[4];
+        node_update<STAGE>(A, sw, j, i0, p, ua);
+        const bool has_b = p + 32 < SEG;
+        if (has_b) node_update<STAGE>(A, sw, j, i0, p + 32, ub);
+        const long long P = A.plane;
+        if (i0 + p < nr) {
+            const long long q = row + i0 + p;
+            A.out[q] = ua[0]; A.out[P + q] = ua[1]; A.out[2 * P + q] = ua[2]; A.out[3 * P + q] = ua[3];
         }
-        // Psi rows: dt (pi - b D_Psi)
-        acc0 = fma(-cb, D0, acc0);
-        acc1 = fma(-cb, D1, acc1);
-        // pi rows: dt (b D_pi + K D_Psi + Bt pi + i Im(C) Psi + theta terms)
-        acc2 = fma(cb, D2, acc2);
-        acc2 = fma(cKr, D0, acc2);
-        acc2 = fma(-cKi, D1, acc2);
-        acc2 = fma(cBr, pir, acc2);
-        acc2 = fma(-cBi, pii, acc2);
-        acc2 = fma(-cCi, psi, acc2);
-        acc3 = fma(cb, D3, acc3);
-        acc3 = fma(cKi, D0, acc3);
-        acc3 = fma(cKr, D1, acc3);
-        acc3 = fma(cBi, pir, acc3);
-        acc3 = fma(cBr, pii, acc3);
-        acc3 = fma(cCi, psr, acc3);
-#pragma unroll
-        for (int k = -2; k <= 2; ++k) {
-            const int jj = min(max(j + k, 0), A.nth - 1);   // weight is 0 off-grid
-            const double w = __ldg(cf + (kW0 + k) * P + i);
-            const long long qq = (long long)jj * nr + i;
-            acc2 = fma(w, __ldg(A.up + qq), acc2);
-            acc3 = fma(w, __ldg(A.up + P + qq), acc3);
+        if (has_b && i0 + p + 32 < nr) {
+            const long long q = row + i0 + p + 32;
+            A.out[q] = ub[0]; A.out[P + q] = ub[1]; A.out[2 * P + q] = ub[2]; A.out[3 * P + q] = ub[3];
         }
-        if (STAGE >= 2) {
-            acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
-            acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
-            acc2 = fma(A.beta, acc2, A.alpha * A.un[2 * P + q]);
-            acc3 = fma(A.beta, acc3, A.alpha * A.un[3 * P + q]);
-        }
-        A.out[q] = acc0;
-        A.out[P + q] = acc1;
-        A.out[2 * P + q] = acc2;
-        A.out[3 * P + q] = acc3;
     }
 #undef DL
 #undef SD
 #undef FL
+}
+
+// eps = m 2^E with m in [1, 2): E, whether m == 1, and the binary32 bits of m
+// rounded (to nearest, ties to even) to the weight format's significand.
+static void eps_parts(double eps, int wprec, int* E, int* pow2, unsigned* mant_bits) {
+    uint64_t b;
+    std::memcpy(&b, &eps, sizeof b);
+    *E = (int)((b >> 52) & 0x7ff) - 1023;
+    const uint64_t m = b & 0xfffffffffffffULL;
+    *pow2 = m == 0;
+    const int P = wprec == TEUK_W_FP16 ? 11 : (wprec == TEUK_W_BF16 ? 8 : 24);
+    const int D = 53 - P;
+    uint64_t kept = m >> D;
+    const uint64_t dropped = m & ((1ULL << D) - 1), half = 1ULL << (D - 1);
+    if (dropped > half || (dropped == half && (kept & 1))) kept += 1;
+    // exponent field 127 (value in [1, 2)); a carry makes it exactly 2
+    *mant_bits = (127u << 23) + (unsigned)(kept << (24 - P));
 }
 
 template <int W>
@@ -369,8 +511,8 @@ cudaError_t launch_stage(const teuk_params& p, const double* coef, const double*
     A.dt = dt;
     A.alpha = stage == 2 ? 0.75 : (stage == 3 ? 1.0 / 3.0 : 0.0);
     A.beta = stage == 2 ? 0.25 : (stage == 3 ? 2.0 / 3.0 : 1.0);
-    A.eps = p.eps;
     A.eps4 = 4.0 * p.eps;
+    eps_parts(p.eps, p.wprec, &A.eps_exp, &A.eps_pow2, &A.eps_mant);
     switch (p.wprec) {
     case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, st);
     case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, st);
