@@ -139,6 +139,28 @@ teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_de
                           double* u_dev, double* work_dev, int64_t nsteps,
                           void* stream);
 
+/* Same computation as teuk_step_dev, for callers that cannot allocate device
+ * memory: code whose device memory is all owned by another allocator (for
+ * example a framework's caching pool that has reserved the GPU, where a
+ * direct cudaMalloc can fail or fragment the pool), and latency-critical loops
+ * where cudaMalloc or cudaFree would synchronise the device. The paper has no
+ * counterpart; this is a deployment convenience.
+ * The two intermediate stage buffers live in a fixed array inside the library
+ * (8 MiB, held by every GPU that loads the library until the process exits),
+ * so ntheta*nr must be <= TEUK_STATIC_MAX_NODES; larger grids return
+ * TEUK_ERR_ARG. The caller still passes inputs and outputs (coef_dev, u_dev).
+ * Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library call.
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture. The array keeps the last call's contents; each step writes every
+ * element of both stage buffers before reading it, so nothing needs to start
+ * at zero. All calls on a device share the one array: calls whose work
+ * overlaps on the GPU (different streams without ordering between them) race
+ * and give wrong results. */
+#define TEUK_STATIC_MAX_NODES 131072
+teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* coef_dev,
+                                 double* u_dev, int64_t nsteps, void* stream);
+
 /* ---- handle API (library-owned device memory) --------------------------- */
 
 /* Allocate the state, stage buffers and coefficient array on the current

@@ -63,6 +63,7 @@ def lib():
             "teuk_build_coefficients": (I, [PP, D, P]),
             "teuk_stage_dev": (I, [PP, D, P, P, P, P, I, P]),
             "teuk_step_dev": (I, [PP, D, P, P, P, I64, P]),
+            "teuk_step_dev_static": (I, [PP, D, P, P, I64, P]),
             "teuk_create": (I, [PP, P, P]),
             "teuk_destroy": (I, [P]),
             "teuk_get_info": (I, [P, PP, P, P]),
@@ -177,6 +178,16 @@ def teuk_stage_dev(p, dt, coef_dev, u_n, u_prev, u_out, stage, stream=None):
 def teuk_step_dev(p, dt, coef_dev, u_dev, work_dev, nsteps, stream=None):
     _check(lib().teuk_step_dev(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_dev),
                                _dptr(work_dev), int(nsteps), _stream(stream)))
+
+
+TEUK_STATIC_MAX_NODES = 131072
+
+
+def teuk_step_dev_static(p, dt, coef_dev, u_dev, nsteps, stream=None):
+    """teuk_step_dev without caller scratch: the stage buffers are a fixed
+    array inside the library (grids up to TEUK_STATIC_MAX_NODES nodes)."""
+    _check(lib().teuk_step_dev_static(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_dev),
+                                      int(nsteps), _stream(stream)))
 
 
 class Handle:

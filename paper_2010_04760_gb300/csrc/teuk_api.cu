@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -108,6 +109,47 @@ teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_de
     for (int64_t k = 0; k < nsteps; ++k)
         TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, work_dev, work_dev + n,
                               (cudaStream_t)stream));
+    clear_error();
+    return TEUK_OK;
+}
+
+// Stage buffers of teuk_step_dev_static: a fixed device array, so that the
+// call allocates nothing. In host code `g_static_stages` is only a host-side
+// stand-in for the array; its device address comes from cudaGetSymbolAddress,
+// looked up once per device (with that device current) and cached.
+constexpr size_t kStaticStageDoubles = 8 * (size_t)TEUK_STATIC_MAX_NODES;  // 2 stages x 4 planes
+static __device__ __align__(256) double g_static_stages[kStaticStageDoubles];
+static std::mutex g_static_mutex;
+static double* g_static_ptr[256] = {nullptr};
+
+teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* coef_dev,
+                                 double* u_dev, int64_t nsteps, void* stream) {
+    teuk_status st = teuk_check_params(p);
+    if (st != TEUK_OK) return st;
+    const size_t nodes = (size_t)p->nr * p->ntheta;
+    if (nodes > (size_t)TEUK_STATIC_MAX_NODES)
+        return fail(TEUK_ERR_ARG, "grid has " + std::to_string(nodes) +
+                                      " nodes; teuk_step_dev_static holds at most " +
+                                      std::to_string(TEUK_STATIC_MAX_NODES));
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+    if (!coef_dev || !u_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
+    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+    int dev = 0;
+    TEUK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(TEUK_ERR_ARG, "device ordinal out of range");
+    double* stages = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ptr[dev]) {
+            void* ptr = nullptr;
+            TEUK_CUDA(cudaGetSymbolAddress(&ptr, g_static_stages));
+            g_static_ptr[dev] = static_cast<double*>(ptr);
+        }
+        stages = g_static_ptr[dev];
+    }
+    const size_t n = 4 * nodes;
+    for (int64_t k = 0; k < nsteps; ++k)
+        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, stages, stages + n, (cudaStream_t)stream));
     clear_error();
     return TEUK_OK;
 }

@@ -1,0 +1,70 @@
+"""teuk_step_dev_static: stepping for callers that cannot allocate device
+memory (for example code whose device memory all belongs to a framework's
+caching pool, or latency-critical loops where cudaMalloc/cudaFree would
+synchronise the device). Its stage buffers are a fixed array inside the
+library. Two calls in a row, on different grids and data, must give what the
+caller-scratch entry point teuk_step_dev gives, within the parity tolerance
+used by the other GPU tests (1e-12 of the largest magnitude per component)."""
+import numpy as np
+import pytest
+
+import paper_2010_04760_gb300 as T
+from paper_2010_04760_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    T.lib()
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _reference_and_static(wl, wprec, nsteps, dt):
+    p = T.params_from_workload(wl, wprec=wprec)
+    coef = _dev(T.teuk_build_coefficients(p, dt))
+    u0 = I.initial_data(wl)
+    u_ref = _dev(u0)
+    work = torch.empty(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    T.teuk_step_dev(p, dt, coef, u_ref, work, nsteps)
+    u_st = _dev(u0)
+    T.teuk_step_dev_static(p, dt, coef, u_st, nsteps)
+    torch.cuda.synchronize()
+    return u_ref.cpu().numpy(), u_st.cpu().numpy()
+
+
+def _close(got, ref):
+    for c in range(4):
+        scale = np.max(np.abs(ref[c]))
+        assert np.max(np.abs(got[c] - ref[c])) <= TOL * scale + 1e-300, c
+
+
+def test_static_scratch_matches_caller_scratch_two_calls():
+    # first call: the 256 x 32 scalar workload, binary32 weights
+    ref, got = _reference_and_static(I.SCHW_SCALAR, "fp32", 7, 0.05)
+    _close(got, ref)
+    # second call on the same array: a different grid at the size limit
+    # (1024 x 128 = TEUK_STATIC_MAX_NODES nodes) and different data
+    wl = I.KERR_GRAV.with_(nr=1024, nth=128, rs_min=-60.0, rs_max=140.0)
+    assert wl.nr * wl.nth == T.TEUK_STATIC_MAX_NODES
+    ref, got = _reference_and_static(wl, "fp64", 5, 0.01)
+    _close(got, ref)
+
+
+def test_static_scratch_rejects_grids_beyond_the_limit():
+    wl = I.KERR_GRAV.with_(nr=1025, nth=128)
+    p = T.params_from_workload(wl)
+    coef = torch.zeros(T.teuk_coeff_count(p), dtype=torch.float64, device="cuda")
+    u = torch.zeros(4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    with pytest.raises(T.TeukError) as ei:
+        T.teuk_step_dev_static(p, 0.01, coef, u, 1)
+    assert ei.value.status == T.TEUK_ERR_ARG
+    assert str(T.TEUK_STATIC_MAX_NODES) in str(ei.value)
