@@ -42,9 +42,27 @@ FP64_FLOPS_PER_PT_STAGE = 112.0
 # algorithmic HBM bytes per point-stage: 11 coefficient planes (88 B), u_prev
 # (32 B), u_out (32 B), u^n in stages 2 and 3 (2/3 x 32 B).
 BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
-# FP64 FMA throughput measured on this GPU type (lane-FMA/s x 2 flops); the
-# nominal figure is 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s.
-FP64_PEAK_TFLOPS_MEASURED = 1.013
+# DRAM bytes (read + write) per launch of the binary32-weight stage kernel,
+# averaged over the three stages, from one ncu capture of this workload
+# (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel source it
+# was taken on, identified by its sha256.
+NCU_TRAFFIC = {"source": "paper_2010_04760_gb300/csrc/teuk_stage.cu",
+               "sha256": "bb5efd8194392ef932f847e06585dd4815ac440aeaecfa0e9f80daf483edfdbe",
+               "bytes_per_launch": (31477504 + 39867392 + 39869696) / 3.0}
+
+
+def ncu_traffic():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, NCU_TRAFFIC["source"]), "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return NCU_TRAFFIC["bytes_per_launch"] if digest == NCU_TRAFFIC["sha256"] else None
+
+
+# Nominal binary64 rate of the part: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS_NOMINAL = 1.259
 
 
 def load_peaks():
@@ -280,6 +298,7 @@ def main():
     e2e_s = max_over_ranks(e2e_s, world, device)
     err, t_err = waveform_error(T, torch, stream) if rank == 0 else (None, None)
 
+    fp64_peak_tf = 2.0 * T.teuk_fp64_fma_rate(stream) / 1e12      # measured live
     pts = POINTS * 3 * args.steps * world
     value = pts / (ms32 * 1e-3)
     value64 = pts / (ms64 * 1e-3)
@@ -303,11 +322,14 @@ def main():
         "mixed_speedup_vs_fp64_weights": value / value64,
         "waveform_rel_l2_fp32_vs_fp64_weights": err,
         "waveform_error_window": f"Psi(r*=50M, all theta) every 100 steps to t={t_err:.1f}M",
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS_MEASURED,
-                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS_MEASURED,
-                     "traffic": None, "pipe": "fp64",
-                     "peak_source": "measured FP64 FMA microbenchmark on GB300 "
-                                    "(profiles/fp64_pipe_microbenchmark.md); nominal 1.26",
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tf,
+                     "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak_tf,
+                     "traffic": ncu_traffic(), "traffic_unit": "bytes per launch",
+                     "algorithmic_bytes_per_launch": BYTES_PER_PT_STAGE * POINTS,
+                     "pipe": "fp64",
+                     "peak_source": "measured: binary64 FMA rate of this GPU from "
+                                    "teuk_fp64_fma_rate (independent FMA chains), x2 flops; "
+                                    f"nominal {FP64_PEAK_TFLOPS_NOMINAL}",
                      "kernel": "stage_kernel<fp32 weights>",
                      "flops_per_point_stage": FP64_FLOPS_PER_PT_STAGE},
         "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",

@@ -113,6 +113,13 @@ size_t teuk_coeff_count(const teuk_params* p);
 teuk_status teuk_build_coefficients(const teuk_params* p, double dt,
                                     double* coef_host);
 
+/* Sustained binary64 FMA throughput of the current device, measured with a
+ * short kernel of independent FMA chains (about 10 ms): *fma_per_s receives
+ * lane-FMAs per second (2 flops each). The paper has no counterpart; this is
+ * the denominator of the binary64 roofline that bounds the stage kernel.
+ * Allocates and frees a small result buffer; synchronises the stream. */
+teuk_status teuk_fp64_fma_rate(void* stream, double* fma_per_s);
+
 /* ---- stateless device entry points (caller-owned device memory) --------- */
 
 /* One fused SSP-RK(3,3) stage (Sec. 3.2) on device arrays:

@@ -64,6 +64,7 @@ def lib():
             "teuk_stage_dev": (I, [PP, D, P, P, P, P, I, P]),
             "teuk_step_dev": (I, [PP, D, P, P, P, I64, P]),
             "teuk_step_dev_static": (I, [PP, D, P, P, I64, P]),
+            "teuk_fp64_fma_rate": (I, [P, P]),
             "teuk_create": (I, [PP, P, P]),
             "teuk_destroy": (I, [P]),
             "teuk_get_info": (I, [P, PP, P, P]),
@@ -178,6 +179,13 @@ def teuk_stage_dev(p, dt, coef_dev, u_n, u_prev, u_out, stage, stream=None):
 def teuk_step_dev(p, dt, coef_dev, u_dev, work_dev, nsteps, stream=None):
     _check(lib().teuk_step_dev(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_dev),
                                _dptr(work_dev), int(nsteps), _stream(stream)))
+
+
+def teuk_fp64_fma_rate(stream=None):
+    """Measured binary64 lane-FMAs per second of the current device."""
+    out = ctypes.c_double()
+    _check(lib().teuk_fp64_fma_rate(_stream(stream), ctypes.byref(out)))
+    return out.value
 
 
 TEUK_STATIC_MAX_NODES = 131072

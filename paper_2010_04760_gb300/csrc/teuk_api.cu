@@ -60,6 +60,18 @@ __global__ void observe_kernel(const double* __restrict__ u, int nr, int nth, lo
     }
 }
 
+// Eight independent FMA chains per thread; one result per thread.
+constexpr int kRateIters = 4096;
+__global__ void fp64_rate_kernel(double* out, double a, double b) {
+    double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+    double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < kRateIters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
 }  // namespace teuk
 
 using namespace teuk;
@@ -150,6 +162,40 @@ teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* 
     const size_t n = 4 * nodes;
     for (int64_t k = 0; k < nsteps; ++k)
         TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, stages, stages + n, (cudaStream_t)stream));
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_fp64_fma_rate(void* stream, double* fma_per_s) {
+    if (!fma_per_s) return fail(TEUK_ERR_ARG, "fma_per_s is NULL");
+    int dev = 0, sms = 0;
+    TEUK_CUDA(cudaGetDevice(&dev));
+    TEUK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, blocks = sms * 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* out = nullptr;
+    TEUK_CUDA(cudaMalloc(&out, sizeof(double) * (size_t)threads * blocks));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) {
+            fp64_rate_kernel<<<blocks, threads, 0, st>>>(out, 0.999999, 1e-7);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "teuk_fp64_fma_rate");
+    *fma_per_s = 8.0 * kRateIters * (double)threads * blocks / (best * 1e-3);
     clear_error();
     return TEUK_OK;
 }

@@ -29,28 +29,30 @@
 
 namespace teuk {
 
-#ifndef TEUK_SEG
-#define TEUK_SEG 64
-#endif
 #ifndef TEUK_WARPS
 #define TEUK_WARPS 4
 #endif
 #ifndef TEUK_MINB
 #define TEUK_MINB 8                // resident CTAs per SM the register budget targets
 #endif
-#define TEUK_BOUNDS __launch_bounds__(TEUK_WARPS * 32, TEUK_MINB)
-#ifndef TEUK_ILP
-#define TEUK_ILP 1                 // interfaces per lane and iteration in the flux phase
-#endif
-#ifndef TEUK_SPLIT
-#define TEUK_SPLIT 0               // theta terms in a separate partial sum
-#endif
-constexpr int SEG = TEUK_SEG;    // r* nodes per warp
 constexpr int WARPS = TEUK_WARPS;  // theta rows per CTA (one per warp)
-constexpr int ND = SEG + 5;      // first differences d_k, k in [i0-3, i0+SEG+1]
-constexpr int NS = SEG + 3;      // s_k, k in [i0-2, i0+SEG]
-constexpr int NF = SEG + 1;      // interfaces i+1/2, i in [i0-1, i0+SEG-1]
-constexpr int NW = ND + NS + NF; // doubles per component per warp
+#define TEUK_BOUNDS __launch_bounds__(TEUK_WARPS * 32, TEUK_MINB)
+
+// r* nodes per warp: 32 with reduced-precision weights, 64 with binary64
+// weights (each the measured best on GB300 for the 2048 x 128 workload).
+template <int W> struct Seg {
+#ifdef TEUK_SEG
+    static constexpr int value = TEUK_SEG;
+#else
+    static constexpr int value = W == TEUK_W_FP64 ? 64 : 32;
+#endif
+};
+// Shared-memory layout of one warp's segment, per component: first
+// differences d_k (k = i0-3 .. i0+S+1), then s_k (k = i0-2 .. i0+S), then
+// flux terms of interfaces i+1/2 (i = i0-1 .. i0+S-1).
+template <int S> struct Geo {
+    static constexpr int SEG = S, ND = S + 5, NS = S + 3, NF = S + 1, NW = ND + NS + NF;
+};
 
 struct StageArgs {
     const double* coef;   // kCoefPlanes planes of nth*nr
@@ -312,11 +314,11 @@ __device__ __forceinline__ double flux6(double x0, double x1, double x2, double 
 // (x = d_{i+2..i-1}) and whose flux term is the negated positive form. The
 // stencil is chosen by integer index and the sign applied to the bit pattern,
 // so that no binary64 instruction is spent on either.
-template <int W>
+template <int W, class G>
 __device__ __forceinline__ double interface_flux(const double* sw, int idx, const StageArgs& A) {
-    const int c = idx / NF, k = idx - c * NF;
-    const double* dl = sw + c * NW;
-    const double* sd = dl + ND;
+    const int c = idx / G::NF, k = idx - c * G::NF;
+    const double* dl = sw + c * G::NW;
+    const double* sd = dl + G::ND;
     const bool neg = c >= 2;
     const double F = flux6<W, false>(dl[neg ? k + 4 : k], dl[neg ? k + 3 : k + 1], dl[k + 2],
                                      dl[neg ? k + 1 : k + 3], sd[neg ? k + 2 : k], sd[k + 1], A);
@@ -327,19 +329,20 @@ __device__ __forceinline__ double interface_flux(const double* sw, int idx, cons
 // Right-hand side and Runge-Kutta combination at node i0 + p of row j
 // (Sec. 2.3, Sec. 3.2). sw holds the segment's first differences and flux
 // terms. Loads use a clamped node index; the caller stores only real nodes.
-template <int STAGE>
+template <int STAGE, class G>
 __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw, int j,
                                             int i0, int p, double out[4]) {
+    constexpr int NW = G::NW, FO = G::ND + G::NS;   // flux terms start at FO
     const int nr = A.nr;
     const int i = min(i0 + p, nr - 1);
     const long long P = A.plane;
     const long long q = (long long)j * nr + i;
     const double* cf = A.coef + q;
     // 6 h D for each component
-    const double D0 = fma(6.0, sw[0 * NW + p + 2], sw[0 * NW + ND + NS + p + 1]) - sw[0 * NW + ND + NS + p];
-    const double D1 = fma(6.0, sw[1 * NW + p + 2], sw[1 * NW + ND + NS + p + 1]) - sw[1 * NW + ND + NS + p];
-    const double D2 = fma(6.0, sw[2 * NW + p + 3], sw[2 * NW + ND + NS + p + 1]) - sw[2 * NW + ND + NS + p];
-    const double D3 = fma(6.0, sw[3 * NW + p + 3], sw[3 * NW + ND + NS + p + 1]) - sw[3 * NW + ND + NS + p];
+    const double D0 = fma(6.0, sw[0 * NW + p + 2], sw[0 * NW + FO + p + 1]) - sw[0 * NW + FO + p];
+    const double D1 = fma(6.0, sw[1 * NW + p + 2], sw[1 * NW + FO + p + 1]) - sw[1 * NW + FO + p];
+    const double D2 = fma(6.0, sw[2 * NW + p + 3], sw[2 * NW + FO + p + 1]) - sw[2 * NW + FO + p];
+    const double D3 = fma(6.0, sw[3 * NW + p + 3], sw[3 * NW + FO + p + 1]) - sw[3 * NW + FO + p];
     const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
     const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
     const double cb = __ldg(cf + kCb * P), cKr = __ldg(cf + kCKr * P);
@@ -367,24 +370,14 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     acc3 = fma(cBi, pir, acc3);
     acc3 = fma(cBr, pii, acc3);
     acc3 = fma(cCi, psr, acc3);
-#if TEUK_SPLIT
-    double th2 = 0.0, th3 = 0.0;
-#else
-    double& th2 = acc2;
-    double& th3 = acc3;
-#endif
 #pragma unroll
     for (int k = -2; k <= 2; ++k) {
         const int jj = min(max(j + k, 0), A.nth - 1);   // weight is 0 off-grid
         const double w = __ldg(cf + (kW0 + k) * P);
         const long long qq = (long long)jj * nr + i;
-        th2 = fma(w, __ldg(A.up + qq), th2);
-        th3 = fma(w, __ldg(A.up + P + qq), th3);
+        acc2 = fma(w, __ldg(A.up + qq), acc2);
+        acc3 = fma(w, __ldg(A.up + P + qq), acc3);
     }
-#if TEUK_SPLIT
-    acc2 += th2;
-    acc3 += th3;
-#endif
     if (STAGE >= 2) {
         acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
         acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
@@ -396,6 +389,8 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
 
 template <int W, int STAGE>
 __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
+    using G = Geo<Seg<W>::value>;
+    constexpr int SEG = G::SEG, ND = G::ND, NS = G::NS, NF = G::NF, NW = G::NW;
     __shared__ double sm[WARPS][4 * NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
@@ -423,39 +418,20 @@ __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
         SD(c, k) = fma(-2.0, DL(c, k + 1), DL(c, k) + DL(c, k + 2));
     }
     __syncwarp();
-    // 3. interface flux terms, i + 1/2 for i = i0-1 .. i0+SEG-1; two
-    //    independent interfaces per lane and iteration for instruction-level
-    //    parallelism
-#if TEUK_ILP == 1
+    // 3. interface flux terms, i + 1/2 for i = i0-1 .. i0+SEG-1
     for (int idx = lane; idx < 4 * NF; idx += 32) {
         const int c = idx / NF;
-        FL(c, idx - c * NF) = interface_flux<W>(sw, idx, A);
+        FL(c, idx - c * NF) = interface_flux<W, G>(sw, idx, A);
     }
-#else
-    for (int idx = lane; idx < 4 * NF; idx += 64) {
-        const int idx2 = idx + 32;
-        const double Fa = interface_flux<W>(sw, idx, A);
-        double Fb = 0.0;
-        if (idx2 < 4 * NF) Fb = interface_flux<W>(sw, idx2, A);
-        {
-            const int c = idx / NF;
-            FL(c, idx - c * NF) = Fa;
-        }
-        if (idx2 < 4 * NF) {
-            const int c = idx2 / NF;
-            FL(c, idx2 - c * NF) = Fb;
-        }
-    }
-#endif
     __syncwarp();
-    // 4. nodes i = i0 .. i0+SEG-1 (two per lane and iteration, computed
-    //    side by side; the second node's loads use a clamped index and its
-    //    store is predicated)
+    // 4. nodes i = i0 .. i0+SEG-1 (two per lane and iteration, computed side
+    //    by side; the second node's loads use a clamped index and its store is
+    //    predicated)
     for (int p = lane; p < SEG; p += 64) {
         double ua[4], ub[4];
-        node_update<STAGE>(A, sw, j, i0, p, ua);
+        node_update<STAGE, G>(A, sw, j, i0, p, ua);
         const bool has_b = p + 32 < SEG;
-        if (has_b) node_update<STAGE>(A, sw, j, i0, p + 32, ub);
+        if (has_b) node_update<STAGE, G>(A, sw, j, i0, p + 32, ub);
         const long long P = A.plane;
         if (i0 + p < nr) {
             const long long q = row + i0 + p;
@@ -490,6 +466,7 @@ static void eps_parts(double eps, int wprec, int* E, int* pow2, unsigned* mant_b
 
 template <int W>
 static cudaError_t launch_stage_w(const StageArgs& A, int stage, cudaStream_t st) {
+    constexpr int SEG = Seg<W>::value;
     dim3 grid((A.nr + SEG - 1) / SEG, (A.nth + WARPS - 1) / WARPS);
     dim3 block(WARPS * 32);
     switch (stage) {
