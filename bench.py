@@ -213,6 +213,31 @@ def time_e2e(T, torch, steps, stream):
     return el, nbytes
 
 
+def time_batch(T, torch, stream, steps=32):
+    """Throughput of the 64-member uneven batch (one persistent launch per RK
+    stage over all members, graph-replayed; ~43 M nodes, state and
+    coefficients ~7.8 GB, far larger than L2)."""
+    wls = I.batch_workloads()
+    ps = [T.params_from_workload(w) for w in wls]
+    b = T.teuk_batch_create(ps, stream, autotune=True)
+    for k, w in enumerate(wls):
+        T.teuk_batch_set_state(b, k, I.initial_data(w), 0.0)
+    T.teuk_batch_step(b, 16)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    T.teuk_batch_step(b, steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, _, seg, ctas = T.teuk_batch_get_info(b, 0)
+    b.close()
+    nodes = sum(w.nr * w.nth for w in wls)
+    return {"value": nodes * 3 * steps / (ms * 1e-3), "unit": UNIT, "members": len(wls),
+            "nodes": nodes, "steps": steps, "ms_per_step": ms / steps, "segment": seg,
+            "ctas_per_sm": ctas, "wprec": "fp32"}
+
+
 def oracle_rate(nsteps_budget_s=12.0, wprec="fp32", max_steps=400):
     """Oracle point-stage updates/s on the workload, over a bounded number of
     RK steps chosen to take about nsteps_budget_s seconds."""
@@ -297,6 +322,7 @@ def main():
     e2e_steps = max(10, args.steps // 4)
     e2e_s = max_over_ranks(e2e_s, world, device)
     err, t_err = waveform_error(T, torch, stream) if rank == 0 else (None, None)
+    batch = time_batch(T, torch, stream) if rank == 0 else None
 
     fp64_peak_tf = 2.0 * T.teuk_fp64_fma_rate(stream) / 1e12      # measured live
     pts = POINTS * 3 * args.steps * world
@@ -337,6 +363,7 @@ def main():
                          "bytes_per_point_stage": BYTES_PER_PT_STAGE},
         "e2e": {"value": POINTS * 3 * e2e_steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "batched_64_uneven_evolutions": batch,
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }

@@ -215,6 +215,36 @@ teuk_status teuk_check_finite(teuk_handle* h);
 /* Device pointer of the state planes (valid until teuk_destroy). */
 teuk_status teuk_state_dev(teuk_handle* h, double** u_dev);
 
+/* ---- batched evolutions ---------------------------------------------------
+ * Many independent evolutions (uneven grids, spins, modes, time steps) advanced
+ * together: each Runge-Kutta stage of all members is one persistent launch over
+ * a device work list of (member, 4-row block, r* segment) tiles, and the steps
+ * are replayed from a captured CUDA graph. The launch boundary orders the
+ * stages (no device-side waits). Every member runs the stage operator of
+ * teuk_stage_dev (Sec. 2.3, 3.1, 3.2) with its own coefficients and dt. */
+
+/* n members with parameters ps[0..n-1] (all with the same wprec and
+ * theta_mode; dt == 0 takes each member's own stability rule). State starts at
+ * zero, t = 0. autotune != 0 times the tile shapes (32- or 64-node segments)
+ * and grid sizes (4 or 8 CTAs per SM) on a synthetic state and keeps the
+ * fastest; otherwise the single-evolution defaults are used. stream as for
+ * teuk_create. Allocates one device pool for all members. */
+teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int autotune,
+                              teuk_batch** out);
+teuk_status teuk_batch_destroy(teuk_batch* b);
+
+/* Member k's planar state u[4][ntheta_k][nr_k] and time (host, synchronous). */
+teuk_status teuk_batch_set_state(teuk_batch* b, int k, const double* u_host, double t);
+teuk_status teuk_batch_get_state(teuk_batch* b, int k, double* u_host, double* t_out);
+
+/* Advance every member by nsteps of its own dt (asynchronous). */
+teuk_status teuk_batch_step(teuk_batch* b, int64_t nsteps);
+
+/* Member k's dt and t; the chosen segment length and CTAs per SM (either
+ * output pointer may be NULL). */
+teuk_status teuk_batch_get_info(const teuk_batch* b, int k, double* dt_out, double* t_out,
+                                int* seg_out, int* ctas_per_sm_out);
+
 #ifdef __cplusplus
 }
 #endif

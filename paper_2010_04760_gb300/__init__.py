@@ -75,6 +75,12 @@ def lib():
             "teuk_observe": (I, [P, D, P, P, P]),
             "teuk_check_finite": (I, [P]),
             "teuk_state_dev": (I, [P, P]),
+            "teuk_batch_create": (I, [PP, I, P, I, P]),
+            "teuk_batch_destroy": (I, [P]),
+            "teuk_batch_set_state": (I, [P, I, P, D]),
+            "teuk_batch_get_state": (I, [P, I, P, P]),
+            "teuk_batch_step": (I, [P, I64]),
+            "teuk_batch_get_info": (I, [P, I, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -275,3 +281,61 @@ def teuk_state_dev(h):
     ptr = ctypes.c_void_p()
     _check(lib().teuk_state_dev(h.ptr, ctypes.byref(ptr)))
     return ptr.value
+
+
+class Batch:
+    """Owner of a teuk_batch*; members keep the order of the parameter list."""
+
+    def __init__(self, ptr, ps):
+        self.ptr = ptr
+        self.ps = list(ps)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.ptr:
+            lib().teuk_batch_destroy(self.ptr)
+            self.ptr = None
+
+
+def teuk_batch_create(ps, stream=None, autotune=True):
+    arr = (teuk_params * len(ps))(*ps)
+    b = ctypes.c_void_p()
+    _check(lib().teuk_batch_create(arr, len(ps), _stream(stream), int(bool(autotune)),
+                                   ctypes.byref(b)))
+    return Batch(b, ps)
+
+
+def teuk_batch_destroy(b):
+    b.close()
+
+
+def teuk_batch_set_state(b, k, u, t=0.0):
+    arr, ptr = _host(u)
+    _check(lib().teuk_batch_set_state(b.ptr, int(k), ptr, float(t)))
+
+
+def teuk_batch_get_state(b, k, out=None):
+    p = b.ps[k]
+    if out is None:
+        out = np.empty((4, p.ntheta, p.nr))
+    t = ctypes.c_double()
+    _check(lib().teuk_batch_get_state(b.ptr, int(k), out.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(t)))
+    return out, t.value
+
+
+def teuk_batch_step(b, nsteps):
+    _check(lib().teuk_batch_step(b.ptr, int(nsteps)))
+
+
+def teuk_batch_get_info(b, k):
+    dt, t = ctypes.c_double(), ctypes.c_double()
+    seg, ctas = ctypes.c_int(), ctypes.c_int()
+    _check(lib().teuk_batch_get_info(b.ptr, int(k), ctypes.byref(dt), ctypes.byref(t),
+                                     ctypes.byref(seg), ctypes.byref(ctas)))
+    return dt.value, t.value, seg.value, ctas.value

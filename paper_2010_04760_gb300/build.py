@@ -60,7 +60,7 @@ def build(force=False, verbose=False, ptxas_info=False):
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
     tmp = LIB + ".tmp"
-    subprocess.check_call([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
+    subprocess.check_call([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -1,6 +1,7 @@
 // C ABI: stateless device entry points, the handle (library-owned memory,
 // CUDA-graph stepping), observation and the non-finite check.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -72,9 +73,35 @@ __global__ void fp64_rate_kernel(double* out, double a, double b) {
     out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// A smooth, non-zero synthetic state (used only to time tile shapes).
+__global__ void synth_state_kernel(double* u, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        u[k] = sin(1e-3 * (double)(k % 100003)) + 0.25;
+}
+
 }  // namespace teuk
 
 using namespace teuk;
+
+struct teuk_batch {
+    int n = 0, wprec = 0;
+    std::vector<teuk_params> p;
+    std::vector<double> dt, t;
+    std::vector<size_t> off;      // member k: u at off[k], w at off[k] + 4 plane, coef after
+    double* pool = nullptr;
+    void* desc = nullptr;
+    long long items = 0;
+    int seg = 32, ctas = 8, sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t exec = nullptr;
+    int chunk = 0;
+    size_t plane(int k) const { return (size_t)p[k].nr * p[k].ntheta; }
+    double* u(int k) const { return pool + off[k]; }
+    double* w(int k) const { return pool + off[k] + 4 * plane(k); }
+    double* coef(int k) const { return pool + off[k] + 12 * plane(k); }
+};
 
 struct teuk_handle {
     teuk_params p;
@@ -197,6 +224,183 @@ teuk_status teuk_fp64_fma_rate(void* stream, double* fma_per_s) {
     if (e != cudaSuccess) return cuda_fail(e, "teuk_fp64_fma_rate");
     *fma_per_s = 8.0 * kRateIters * (double)threads * blocks / (best * 1e-3);
     clear_error();
+    return TEUK_OK;
+}
+
+static cudaError_t batch_upload(teuk_batch* b, int seg) {
+    std::vector<BatchEvo> ev(b->n);
+    for (int k = 0; k < b->n; ++k) ev[k] = BatchEvo{b->p[k], b->coef(k), b->u(k), b->w(k), b->dt[k]};
+    return upload_batch_desc(ev.data(), b->n, seg, b->desc, &b->items, b->stream);
+}
+
+static cudaError_t batch_launch_step(teuk_batch* b) {
+    const int grid = b->sms * b->ctas;
+    cudaError_t e = cudaSuccess;
+    for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage)
+        e = launch_batch_stage(b->wprec, stage, b->seg, b->desc, b->n, b->items, grid, b->stream);
+    return e;
+}
+
+teuk_status teuk_batch_destroy(teuk_batch* b) {
+    if (!b) return TEUK_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaFree(b->pool);
+    cudaFree(b->desc);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return TEUK_OK;
+}
+
+teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int autotune,
+                              teuk_batch** out) {
+    if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ps || n < 1) return fail(TEUK_ERR_ARG, "need n >= 1 parameter sets");
+    for (int k = 0; k < n; ++k) {
+        teuk_status st = teuk_check_params(&ps[k]);
+        if (st != TEUK_OK) return fail(st, "member " + std::to_string(k) + ": " + teuk_last_error());
+        if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode)
+            return fail(TEUK_ERR_ARG, "all members need the same wprec and theta_mode");
+    }
+    teuk_batch* b = new teuk_batch();
+    b->n = n;
+    b->wprec = ps[0].wprec;
+    b->p.assign(ps, ps + n);
+    b->dt.resize(n);
+    b->t.assign(n, 0.0);
+    b->off.resize(n);
+    size_t total = 0, max_plane = 0;
+    for (int k = 0; k < n; ++k) {
+        teuk_status st = teuk_stable_dt(&ps[k], &b->dt[k]);
+        if (st != TEUK_OK) { delete b; return st; }
+        b->off[k] = total;
+        total += ((23 * b->plane(k) + 31) / 32) * 32;          // 256-byte aligned members
+        max_plane = std::max(max_plane, b->plane(k));
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if (stream) {
+            b->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->pool, total * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->desc, batch_desc_bytes(n));
+    std::vector<double> host((size_t)kCoefPlanes * max_plane);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        teuk_status st = teuk_build_coefficients(&ps[k], b->dt[k], host.data());
+        if (st != TEUK_OK) { teuk_batch_destroy(b); return st; }
+        e = cudaMemcpyAsync(b->coef(k), host.data(), kCoefPlanes * b->plane(k) * sizeof(double),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host buffer is reused
+    }
+    b->seg = b->wprec == TEUK_W_FP64 ? 64 : 32;
+    b->ctas = 8;
+    if (e == cudaSuccess && autotune) {
+        // time every (segment, CTAs per SM) candidate on a synthetic state
+        for (int k = 0; k < n && e == cudaSuccess; ++k) {
+            synth_state_kernel<<<b->sms * 4, 256, 0, b->stream>>>(b->u(k), 4 * (long long)b->plane(k));
+            e = cudaGetLastError();
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best = -1.0f;
+        int best_seg = b->seg, best_ctas = b->ctas;
+        const int segs[2] = {32, 64}, ctas[2] = {4, 8};
+        for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+            e = batch_upload(b, segs[a]);
+            for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+                b->seg = segs[a];
+                b->ctas = ctas[c];
+                e = batch_launch_step(b);                                  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = batch_launch_step(b);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && (best < 0.0f || ms < best)) {
+                    best = ms; best_seg = segs[a]; best_ctas = ctas[c];
+                }
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        b->seg = best_seg;
+        b->ctas = best_ctas;
+    }
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+        e = cudaMemsetAsync(b->u(k), 0, 4 * b->plane(k) * sizeof(double), b->stream);
+    if (e == cudaSuccess) e = batch_upload(b, b->seg);
+    if (e != cudaSuccess) {
+        teuk_batch_destroy(b);
+        return cuda_fail(e, "teuk_batch_create");
+    }
+    *out = b;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_batch_set_state(teuk_batch* b, int k, const double* u_host, double t) {
+    if (!b || !u_host || k < 0 || k >= (b ? b->n : 0)) return fail(TEUK_ERR_ARG, "bad argument");
+    TEUK_CUDA(cudaMemcpyAsync(b->u(k), u_host, 4 * b->plane(k) * sizeof(double),
+                              cudaMemcpyHostToDevice, b->stream));
+    TEUK_CUDA(cudaStreamSynchronize(b->stream));
+    b->t[k] = t;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_batch_get_state(teuk_batch* b, int k, double* u_host, double* t_out) {
+    if (!b || !u_host || k < 0 || k >= (b ? b->n : 0)) return fail(TEUK_ERR_ARG, "bad argument");
+    TEUK_CUDA(cudaMemcpyAsync(u_host, b->u(k), 4 * b->plane(k) * sizeof(double),
+                              cudaMemcpyDeviceToHost, b->stream));
+    TEUK_CUDA(cudaStreamSynchronize(b->stream));
+    if (t_out) *t_out = b->t[k];
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_batch_step(teuk_batch* b, int64_t nsteps) {
+    if (!b) return fail(TEUK_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+    const int kChunk = 16;
+    if (nsteps >= kChunk && !b->exec) {
+        cudaGraph_t g = nullptr;
+        TEUK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kChunk && e == cudaSuccess; ++k) e = batch_launch_step(b);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+        b->chunk = kChunk;
+    }
+    int64_t left = nsteps;
+    while (b->exec && left >= b->chunk) {
+        TEUK_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        left -= b->chunk;
+    }
+    for (; left > 0; --left) TEUK_CUDA(batch_launch_step(b));
+    for (int k = 0; k < b->n; ++k) b->t[k] += (double)nsteps * b->dt[k];
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_batch_get_info(const teuk_batch* b, int k, double* dt_out, double* t_out,
+                                int* seg_out, int* ctas_per_sm_out) {
+    if (!b || k < 0 || k >= b->n) return fail(TEUK_ERR_ARG, "bad argument");
+    if (dt_out) *dt_out = b->dt[k];
+    if (t_out) *t_out = b->t[k];
+    if (seg_out) *seg_out = b->seg;
+    if (ctas_per_sm_out) *ctas_per_sm_out = b->ctas;
     return TEUK_OK;
 }
 

@@ -1,8 +1,10 @@
 // Host side of the library: parameter validation, the Kerr coefficient
 // generator, the time-step rule and error reporting. binary64 throughout.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "teuk_internal.h"
@@ -82,9 +84,13 @@ double r_of_rstar(double rstar, double M, double a, double* x_out) {
 //   C  = [Delta (s - (m + s cos)^2/sin^2) + 4 i s m a (r-M)]/Sigma^2,
 //   Ath = Delta/Sigma^2, Bth = Delta cot/Sigma^2.
 PointCoef point_coefficients(double rstar, double theta, const teuk_params& p) {
-    const double M = p.M, a = p.a, s = p.s, m = p.m;
     double x;
-    const double r = r_of_rstar(rstar, M, a, &x);
+    const double r = r_of_rstar(rstar, p.M, p.a, &x);
+    return point_coefficients_rx(r, x, theta, p);
+}
+
+PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_params& p) {
+    const double M = p.M, a = p.a, s = p.s, m = p.m;
     Tortoise T(M, a);
     const double Delta = x * (x + T.w);
     const double varpi = r * r + a * a;
@@ -109,6 +115,29 @@ PointCoef point_coefficients(double rstar, double theta, const teuk_params& p) {
     c.Ath = Delta * inv;
     c.Bth = Delta * (cs / sn) * inv;
     return c;
+}
+
+// r and r - r_+ at every r* node.
+static void radial_nodes(const teuk_params& p, std::vector<double>& r, std::vector<double>& x) {
+    const double h = (p.rstar_max - p.rstar_min) / (p.nr - 1);
+    r.resize(p.nr);
+    x.resize(p.nr);
+    for (int i = 0; i < p.nr; ++i) r[i] = r_of_rstar(p.rstar_min + i * h, p.M, p.a, &x[i]);
+}
+
+// Runs body(j0, j1) over theta-row ranges on up to hardware_concurrency threads.
+template <class F>
+static void for_rows(int nth, long long work, F body) {
+    unsigned nt = std::thread::hardware_concurrency();
+    if (nt == 0) nt = 1;
+    if (work < (1LL << 16)) nt = 1;
+    nt = std::min<unsigned>(nt, (unsigned)nth);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; ++t) {
+        const int j0 = (int)((long long)nth * t / nt), j1 = (int)((long long)nth * (t + 1) / nt);
+        pool.emplace_back(body, j0, j1);
+    }
+    for (auto& th : pool) th.join();
 }
 
 }  // namespace teuk
@@ -161,16 +190,23 @@ teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
     if (p->dt > 0.0) { *dt_out = p->dt; return TEUK_OK; }
     const double h = (p->rstar_max - p->rstar_min) / (p->nr - 1);
     const double dth = M_PI / p->ntheta;
-    double lam = 0.0;
-    for (int i = 0; i < p->nr; ++i) {
-        const double rs = p->rstar_min + i * h;
-        for (int j = 0; j < p->ntheta; ++j) {
-            PointCoef c = point_coefficients(rs, (j + 0.5) * dth, *p);
-            double kappa = c.Ath * (16.0 / 3.0) / (dth * dth) + std::fabs(c.Bth) * 1.5 / dth +
-                           std::hypot(c.Cr, c.Ci);
-            lam = std::fmax(lam, c.b / h + std::sqrt(kappa));
+    std::vector<double> r, x;
+    radial_nodes(*p, r, x);
+    std::vector<double> row_lam(p->ntheta, 0.0);
+    for_rows(p->ntheta, (long long)p->nr * p->ntheta, [&](int j0, int j1) {
+        for (int j = j0; j < j1; ++j) {
+            double lam = 0.0;
+            for (int i = 0; i < p->nr; ++i) {
+                PointCoef c = point_coefficients_rx(r[i], x[i], (j + 0.5) * dth, *p);
+                double kappa = c.Ath * (16.0 / 3.0) / (dth * dth) + std::fabs(c.Bth) * 1.5 / dth +
+                               std::hypot(c.Cr, c.Ci);
+                lam = std::fmax(lam, c.b / h + std::sqrt(kappa));
+            }
+            row_lam[j] = lam;
         }
-    }
+    });
+    double lam = 0.0;
+    for (double v : row_lam) lam = std::fmax(lam, v);
     *dt_out = p->cfl / lam;
     return TEUK_OK;
 }
@@ -191,10 +227,13 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
     const double dth = M_PI / nth;
     const double sigma = ((p->m + p->s) % 2 == 0) ? 1.0 : -1.0;   // pole parity
     const double c6h = dt / (6.0 * h);
-    for (int j = 0; j < nth; ++j) {
+    std::vector<double> r, x;
+    radial_nodes(*p, r, x);
+    for_rows(nth, (long long)nr * nth, [&](int j0, int j1) {
+    for (int j = j0; j < j1; ++j) {
         const double th = (j + 0.5) * dth;
         for (int i = 0; i < nr; ++i) {
-            PointCoef c = point_coefficients(p->rstar_min + i * h, th, *p);
+            PointCoef c = point_coefficients_rx(r[i], x[i], th, *p);
             const size_t q = (size_t)j * nr + i;
             coef[kCb * plane + q] = c6h * c.b;
             coef[kCKr * plane + q] = c6h * c.Kr;
@@ -223,6 +262,7 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
             for (int k = 0; k < 5; ++k) coef[(kWm2 + k) * plane + q] = w[k];
         }
     }
+    });
     return TEUK_OK;
 }
 

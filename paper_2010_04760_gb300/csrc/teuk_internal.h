@@ -25,5 +25,27 @@ struct PointCoef {
 };
 double r_of_rstar(double rstar, double M, double a, double* x_out);
 PointCoef point_coefficients(double rstar, double theta, const teuk_params& p);
+PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_params& p);
+
+// Batched evolutions: pointers and step of one member.
+struct BatchEvo {
+    teuk_params p;
+    const double* coef;
+    double* u;
+    double* w;
+    double dt;
+};
+long long batch_items(const teuk_params& p, int segv);
+size_t batch_desc_bytes(int n);
 
 }  // namespace teuk
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+namespace teuk {
+cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_desc,
+                              long long* items_out, cudaStream_t st);
+cudaError_t launch_batch_stage(int wprec, int stage, int segv, const void* d_desc, int n,
+                               long long items, int grid, cudaStream_t st);
+}  // namespace teuk
+#endif

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "teuk_internal.h"
 
@@ -387,18 +388,16 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     out[0] = acc0; out[1] = acc1; out[2] = acc2; out[3] = acc3;
 }
 
-template <int W, int STAGE>
-__global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
-    using G = Geo<Seg<W>::value>;
+// One warp's work: segment seg_blk (nodes seg_blk*SEG ..) of theta row j of
+// the evolution described by A. sw is the warp's shared-memory block.
+template <int W, int STAGE, int SEGV>
+__device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, int lane, int j,
+                                                int seg_blk) {
+    using G = Geo<SEGV>;
     constexpr int SEG = G::SEG, ND = G::ND, NS = G::NS, NF = G::NF, NW = G::NW;
-    __shared__ double sm[WARPS][4 * NW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.y * WARPS + warp;
-    if (j >= A.nth) return;
     const int nr = A.nr;
-    const int i0 = blockIdx.x * SEG;
+    const int i0 = seg_blk * SEG;
     const long long row = (long long)j * nr;
-    double* sw = sm[warp];
 #define DL(c, k) sw[(c) * NW + (k)]
 #define SD(c, k) sw[(c) * NW + ND + (k)]
 #define FL(c, k) sw[(c) * NW + ND + NS + (k)]
@@ -445,6 +444,66 @@ __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
 #undef DL
 #undef SD
 #undef FL
+}
+
+// Single evolution: blockIdx.x = segment, blockIdx.y = block of WARPS rows.
+template <int W, int STAGE>
+__global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
+    constexpr int SEGV = Seg<W>::value;
+    __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.y * WARPS + warp;
+    if (j >= A.nth) return;
+    process_segment<W, STAGE, SEGV>(A, sm[warp], lane, j, blockIdx.x);
+}
+
+// Batched evolutions: one work item is a block of WARPS rows x one segment of
+// one evolution; items of all evolutions are numbered consecutively
+// (item0[k] = first item of evolution k) and a persistent grid walks them.
+// All evolutions advance the same Runge-Kutta stage in one launch; the launch
+// boundary is the stage barrier.
+struct BatchDesc {
+    const double* coef;
+    double* u;            // state
+    double* w;            // two stage buffers (4 planes each)
+    int nr, nth, nseg;
+    long long plane;
+    long long item0;      // first work item of this evolution
+    double dt, eps4;
+    int eps_exp, eps_pow2;
+    unsigned eps_mant;
+};
+
+template <int W, int STAGE, int SEGV>
+__global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, int n,
+                                               long long items) {
+    __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        int lo = 0, hi = n - 1;                 // last k with item0 <= it
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (D[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        const BatchDesc& d = D[lo];
+        const long long local = it - d.item0;
+        const int seg_blk = (int)(local % d.nseg);
+        const int j = (int)(local / d.nseg) * WARPS + warp;
+        if (j < d.nth) {
+            StageArgs A;
+            A.coef = d.coef;
+            A.nr = d.nr; A.nth = d.nth; A.plane = d.plane;
+            A.dt = d.dt; A.eps4 = d.eps4;
+            A.eps_exp = d.eps_exp; A.eps_pow2 = d.eps_pow2; A.eps_mant = d.eps_mant;
+            double* w1 = d.w;
+            double* w2 = d.w + 4 * d.plane;
+            if (STAGE == 1) { A.un = nullptr; A.up = d.u; A.out = w1; A.alpha = 0.0; A.beta = 1.0; }
+            if (STAGE == 2) { A.un = d.u; A.up = w1; A.out = w2; A.alpha = 0.75; A.beta = 0.25; }
+            if (STAGE == 3) { A.un = d.u; A.up = w2; A.out = d.u; A.alpha = 1.0 / 3.0; A.beta = 2.0 / 3.0; }
+            process_segment<W, STAGE, SEGV>(A, sm[warp], lane, j, seg_blk);
+        }
+        __syncwarp();
+    }
 }
 
 // eps = m 2^E with m in [1, 2): E, whether m == 1, and the binary32 bits of m
@@ -495,6 +554,68 @@ cudaError_t launch_stage(const teuk_params& p, const double* coef, const double*
     case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, st);
     case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, st);
     default: return launch_stage_w<TEUK_W_BF16>(A, stage, st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched evolutions (host side).
+// ---------------------------------------------------------------------------
+
+long long batch_items(const teuk_params& p, int segv) {
+    return (long long)((p.nr + segv - 1) / segv) * ((p.ntheta + WARPS - 1) / WARPS);
+}
+
+cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_desc,
+                              long long* items_out, cudaStream_t st) {
+    std::vector<BatchDesc> h(n);
+    long long item = 0;
+    for (int k = 0; k < n; ++k) {
+        const teuk_params& p = evos[k].p;
+        BatchDesc& d = h[k];
+        d.coef = evos[k].coef; d.u = evos[k].u; d.w = evos[k].w;
+        d.nr = p.nr; d.nth = p.ntheta; d.nseg = (p.nr + segv - 1) / segv;
+        d.plane = (long long)p.nr * p.ntheta;
+        d.item0 = item;
+        d.dt = evos[k].dt; d.eps4 = 4.0 * p.eps;
+        eps_parts(p.eps, p.wprec, &d.eps_exp, &d.eps_pow2, &d.eps_mant);
+        item += batch_items(p, segv);
+    }
+    *items_out = item;
+    cudaError_t e = cudaMemcpyAsync(d_desc, h.data(), sizeof(BatchDesc) * n,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+size_t batch_desc_bytes(int n) { return sizeof(BatchDesc) * (size_t)n; }
+
+template <int W, int SEGV>
+static cudaError_t launch_batch_ws(int stage, const BatchDesc* d, int n, long long items,
+                                   int grid, cudaStream_t st) {
+    const dim3 block(WARPS * 32);
+    switch (stage) {
+    case 1: batch_stage_kernel<W, 1, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
+    case 2: batch_stage_kernel<W, 2, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
+    default: batch_stage_kernel<W, 3, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_batch_w(int stage, int segv, const BatchDesc* d, int n, long long items,
+                                  int grid, cudaStream_t st) {
+    return segv == 64 ? launch_batch_ws<W, 64>(stage, d, n, items, grid, st)
+                      : launch_batch_ws<W, 32>(stage, d, n, items, grid, st);
+}
+
+cudaError_t launch_batch_stage(int wprec, int stage, int segv, const void* d_desc, int n,
+                               long long items, int grid, cudaStream_t st) {
+    const BatchDesc* d = static_cast<const BatchDesc*>(d_desc);
+    switch (wprec) {
+    case TEUK_W_FP64: return launch_batch_w<TEUK_W_FP64>(stage, segv, d, n, items, grid, st);
+    case TEUK_W_FP32: return launch_batch_w<TEUK_W_FP32>(stage, segv, d, n, items, grid, st);
+    case TEUK_W_FP16: return launch_batch_w<TEUK_W_FP16>(stage, segv, d, n, items, grid, st);
+    default: return launch_batch_w<TEUK_W_BF16>(stage, segv, d, n, items, grid, st);
     }
 }
 
