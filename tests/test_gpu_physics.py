@@ -1,0 +1,100 @@
+"""Accuracy of the reduced-precision weights and physics of GPU evolutions.
+
+Stated bounds (relative L2 against the same run with binary64 weights, each
+about 5x the value measured on GB300):
+  Kerr a = 0.999 M, s = -2, m = 2, 2048 x 128, Psi(r* = 50 M, all theta)
+  every 100 steps to t = 150 M: binary32 1e-9, binary16 1e-5, bfloat16 1e-4.
+  Extremal scalar, 8192 x 256, to t = 100 M, the horizon gather (Psi, pi,
+  dPsi/dr* at the innermost node): binary32 1e-9, binary16 1e-5, bfloat16 1e-4.
+Price tail: the local index p = t dPsi/dt / Psi at r* = 20 M of an l = 0
+scalar pulse (a = 0) tends to -3 (Sec. 3, Sec. 4); the GPU reproduces the
+oracle's p(t)."""
+import numpy as np
+import pytest
+
+import oracle as o
+import paper_2010_04760_gb300 as T
+from paper_2010_04760_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    T.lib()
+
+
+def _series(wl, wprec, t_end, r_ext, every):
+    h = T.teuk_create(T.params_from_workload(wl, wprec=wprec))
+    T.teuk_set_state(h, I.initial_data(wl), 0.0)
+    _, dt, _ = T.teuk_get_info(h)
+    ws, hs = [], []
+    for _ in range(max(1, int(t_end / dt) // every)):
+        T.teuk_step(h, every)
+        w, hz, _ = T.teuk_observe(h, r_ext)
+        ws.append(w.copy())
+        hs.append(hz.copy())
+    h.close()
+    return np.array(ws), np.array(hs)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_waveform_error_of_reduced_weights_kerr():
+    ref, _ = _series(I.KERR_GRAV, "fp64", 150.0, 50.0, 100)
+    for wprec, bound in (("fp32", 1e-9), ("fp16", 1e-5), ("bf16", 1e-4)):
+        w, _ = _series(I.KERR_GRAV, wprec, 150.0, 50.0, 100)
+        err = _rel(w, ref)
+        assert err <= bound, (wprec, err)
+
+
+def test_horizon_drift_of_reduced_weights_extremal():
+    _, ref = _series(I.EXTREMAL_SCALAR, "fp64", 100.0, 10.0, 500)
+    for wprec, bound in (("fp32", 1e-9), ("fp16", 1e-5), ("bf16", 1e-4)):
+        _, hz = _series(I.EXTREMAL_SCALAR, wprec, 100.0, 10.0, 500)
+        err = _rel(hz, ref)
+        assert err <= bound, (wprec, err)
+
+
+def test_price_tail_on_gpu_matches_oracle():
+    L, h, T_end = 400.0, 0.5, 650.0
+    nr, nth = int(round(2 * L / h)) + 1, 6
+    wl = I.Workload(name="tail", nr=nr, nth=nth, rs_min=-L, rs_max=L, rc=0.0, width=4.0,
+                    ells=(0,), seed=0)
+    dt = 0.4 * h
+    chunk = int(round(10.0 / dt))
+    nchunks = int(T_end / (chunk * dt))
+
+    def index(ts, ps):
+        ts, ps = np.array(ts), np.array(ps)
+        p = ts[1:-1] * (ps[2:] - ps[:-2]) / (ts[2:] - ts[:-2]) / ps[1:-1]
+        return p[ts[1:-1] > 250.0]
+
+    g = o.grid(nr, nth, -L, L, 1.0, 0.0, 0, 0, 1e-6, "fp64")
+    co = o.coefficients(g)
+    u = I.initial_data(wl)
+    ie = int(round((20.0 + L) / h))
+    ts, ps = [], []
+    for k in range(nchunks):
+        u = o.rk3_step(g, co, dt, u, chunk)
+        ts.append((k + 1) * chunk * dt)
+        ps.append(u[0, 0, ie])
+    p_oracle = index(ts, ps)
+    assert np.all(np.abs(p_oracle + 3.0) < 0.1)
+    for wprec, tol in (("fp64", 1e-8), ("fp32", 1e-4), ("fp16", 0.1)):
+        hd = T.teuk_create(T.params_from_workload(wl, wprec=wprec, dt=dt))
+        T.teuk_set_state(hd, I.initial_data(wl), 0.0)
+        ts, ps = [], []
+        for _ in range(nchunks):
+            T.teuk_step(hd, chunk)
+            wv, _, t = T.teuk_observe(hd, 20.0)
+            ts.append(t)
+            ps.append(wv[0, 0])
+        p = index(ts, ps)
+        assert np.all(np.abs(p + 3.0) < 0.1), (wprec, p)
+        assert np.max(np.abs(p - p_oracle)) < tol, (wprec, np.max(np.abs(p - p_oracle)))
