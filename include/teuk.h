@@ -57,7 +57,12 @@ typedef enum {
 
 /* Discretisation of the theta derivatives (Sec. 3.1). */
 typedef enum {
-    TEUK_THETA_CENTERED4 = 0   /* fourth-order centred, the paper's choice      */
+    TEUK_THETA_CENTERED4 = 0,  /* fourth-order centred, the paper's choice      */
+    TEUK_THETA_WENO5 = 1       /* option: the first theta derivative by WENO5,
+                                  upwinded by the sign of -Bth (its speed when
+                                  the term is read as -(-Bth) dPsi/dtheta), with
+                                  the r* weight precision; the second derivative
+                                  stays fourth-order centred */
 } teuk_theta_mode;
 
 /* Problem statement (Sec. 2.1-2.3, Sec. 4): grid, domain, black hole, mode.
@@ -101,7 +106,7 @@ teuk_status teuk_check_params(const teuk_params* p);
 teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out);
 
 /* Number of doubles in the kernel coefficient array of p (11 planes of
- * ntheta*nr). 0 if p is invalid. */
+ * ntheta*nr, 12 with TEUK_THETA_WENO5). 0 if p is invalid. */
 size_t teuk_coeff_count(const teuk_params* p);
 
 /* Kernel coefficient array for time step dt, written to host memory

@@ -39,7 +39,8 @@ class Grid(ctypes.Structure):
                 ("rs_min", ctypes.c_double), ("rs_max", ctypes.c_double),
                 ("M", ctypes.c_double), ("a", ctypes.c_double),
                 ("s", ctypes.c_int), ("m", ctypes.c_int),
-                ("eps", ctypes.c_double), ("wprec", ctypes.c_int)]
+                ("eps", ctypes.c_double), ("wprec", ctypes.c_int),
+                ("theta_mode", ctypes.c_int)]
 
 
 def _load():
@@ -80,9 +81,9 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def grid(nr, nth, rs_min, rs_max, M=1.0, a=0.0, s=0, m=0, eps=1e-6, wprec="fp64"):
+def grid(nr, nth, rs_min, rs_max, M=1.0, a=0.0, s=0, m=0, eps=1e-6, wprec="fp64", theta_mode=0):
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
-    return Grid(nr, nth, rs_min, rs_max, M, a, s, m, eps, w)
+    return Grid(nr, nth, rs_min, rs_max, M, a, s, m, eps, w, int(theta_mode))
 
 
 def num_threads():

@@ -16,7 +16,11 @@
  *    extrapolation). theta: cell-centred grid, ghost rows mirror across the
  *    poles with parity (-1)^(m+s).
  *  - theta derivatives: fourth-order centred differences (the paper says
- *    "standard centered differencing" without an order).
+ *    "standard centered differencing" without an order). Optional theta WENO
+ *    (theta_mode 1): the first derivative in the Bth term is the WENO5
+ *    derivative along theta, upwinded by the sign of the term's speed -Bth
+ *    (the term read as -(-Bth) dPsi/dtheta), with weights in the same
+ *    precision as in r*; the second derivative stays centred.
  *  - Reduced-precision weights: first differences formed in binary64, scaled
  *    by a power of two, rounded to the weight format; smoothness indicators,
  *    epsilon, alpha and omega computed in that format with every operation
@@ -368,6 +372,31 @@ void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) 
             }
             double complex psi_th = (nb[0] - 8.0 * nb[1] + 8.0 * nb[3] - nb[4])
                                     / (12.0 * dth);
+            if (g->theta_mode == 1) {
+                /* WENO5 along theta: rows j-3 .. j+3 with parity ghosts */
+                double line[2][7];
+                for (int k = -3; k <= 3; ++k) {
+                    int jj = j + k;
+                    double sg = 1.0;
+                    if (jj < 0) { jj = -1 - jj; sg = sigma; }
+                    if (jj >= nth) { jj = 2 * nth - 1 - jj; sg = sigma; }
+                    long q = (long)jj * nr + i;
+                    line[0][k + 3] = sg * u[0 * plane + q];
+                    line[1][k + 3] = sg * u[1 * plane + q];
+                }
+                double Bth_here = coef[8 * plane + p];
+                int dir = (-Bth_here < 0.0) ? -1 : +1;
+                double d[2];
+                for (int c = 0; c < 2; ++c) {
+                    /* interfaces j+1/2 and j-1/2 */
+                    const double* sp = (dir > 0) ? &line[c][1] : &line[c][2];
+                    const double* sm = (dir > 0) ? &line[c][0] : &line[c][1];
+                    double fp = orc_weno5_flux(g->wprec, dir, sp, g->eps, NULL, NULL, NULL);
+                    double fm = orc_weno5_flux(g->wprec, dir, sm, g->eps, NULL, NULL, NULL);
+                    d[c] = (fp - fm) / dth;
+                }
+                psi_th = d[0] + I * d[1];
+            }
             double complex psi_thth = (-nb[0] + 16.0 * nb[1] - 30.0 * nb[2]
                                        + 16.0 * nb[3] - nb[4]) / (12.0 * dth * dth);
             double b = coef[0 * plane + p];

@@ -32,6 +32,7 @@ typedef struct {
     int s, m;                /* spin weight and azimuthal mode number            */
     double eps;              /* WENO epsilon                                     */
     int wprec;               /* weight precision code                            */
+    int theta_mode;          /* 0: centred dtheta; 1: WENO5 dtheta (reading)     */
 } orc_grid;
 
 double orc_rstar_of_r(double r, double M, double a);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libteuk.so")
 
 TEUK_OK, TEUK_ERR_ARG, TEUK_ERR_CUDA, TEUK_ERR_NONFINITE, TEUK_ERR_TIMEOUT, TEUK_ERR_STATE = range(6)
 TEUK_W_FP64, TEUK_W_FP32, TEUK_W_FP16, TEUK_W_BF16 = range(4)
-TEUK_THETA_CENTERED4 = 0
+TEUK_THETA_CENTERED4, TEUK_THETA_WENO5 = 0, 1
 WPREC = {"fp64": TEUK_W_FP64, "fp32": TEUK_W_FP32, "fp16": TEUK_W_FP16, "bf16": TEUK_W_BF16}
 COEF_PLANES = 11
 
@@ -172,7 +172,7 @@ def teuk_build_coefficients(p, dt):
     n = teuk_coeff_count(p)
     if n == 0:
         _check(lib().teuk_check_params(ctypes.byref(p)))
-    out = np.zeros((COEF_PLANES, p.ntheta, p.nr))
+    out = np.zeros((n // (p.ntheta * p.nr), p.ntheta, p.nr))
     _check(lib().teuk_build_coefficients(ctypes.byref(p), dt, out.ctypes.data_as(ctypes.c_void_p)))
     return out
 

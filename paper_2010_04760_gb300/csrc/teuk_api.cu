@@ -237,7 +237,8 @@ static cudaError_t batch_launch_step(teuk_batch* b) {
     const int grid = b->sms * b->ctas;
     cudaError_t e = cudaSuccess;
     for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage)
-        e = launch_batch_stage(b->wprec, stage, b->seg, b->desc, b->n, b->items, grid, b->stream);
+        e = launch_batch_stage(b->wprec, b->p[0].theta_mode, stage, b->seg, b->desc, b->n,
+                               b->items, grid, b->stream);
     return e;
 }
 
@@ -274,7 +275,7 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
         teuk_status st = teuk_stable_dt(&ps[k], &b->dt[k]);
         if (st != TEUK_OK) { delete b; return st; }
         b->off[k] = total;
-        total += ((23 * b->plane(k) + 31) / 32) * 32;          // 256-byte aligned members
+        total += (((12 + coef_planes(ps[k].theta_mode)) * b->plane(k) + 31) / 32) * 32;  // aligned
         max_plane = std::max(max_plane, b->plane(k));
     }
     int dev = 0;
@@ -290,11 +291,12 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->pool, total * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->desc, batch_desc_bytes(n));
-    std::vector<double> host((size_t)kCoefPlanes * max_plane);
+    const int planes = coef_planes(ps[0].theta_mode);
+    std::vector<double> host((size_t)planes * max_plane);
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
         teuk_status st = teuk_build_coefficients(&ps[k], b->dt[k], host.data());
         if (st != TEUK_OK) { teuk_batch_destroy(b); return st; }
-        e = cudaMemcpyAsync(b->coef(k), host.data(), kCoefPlanes * b->plane(k) * sizeof(double),
+        e = cudaMemcpyAsync(b->coef(k), host.data(), planes * b->plane(k) * sizeof(double),
                             cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host buffer is reused
     }
@@ -427,7 +429,7 @@ teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
     st = teuk_stable_dt(p, &h->dt);
     if (st != TEUK_OK) { delete h; return st; }
     const size_t n = h->plane();
-    std::vector<double> coef((size_t)kCoefPlanes * n);
+    std::vector<double> coef((size_t)coef_planes(p->theta_mode) * n);
     st = teuk_build_coefficients(p, h->dt, coef.data());
     if (st != TEUK_OK) { delete h; return st; }
     cudaError_t e = cudaSuccess;

@@ -176,7 +176,8 @@ teuk_status teuk_check_params(const teuk_params* p) {
     if (!(p->eps >= 1e-60 && p->eps <= 1.0)) return fail(TEUK_ERR_ARG, "eps must be in [1e-60, 1]");
     if (p->wprec < TEUK_W_FP64 || p->wprec > TEUK_W_BF16)
         return fail(TEUK_ERR_ARG, "unknown weight precision");
-    if (p->theta_mode != TEUK_THETA_CENTERED4) return fail(TEUK_ERR_ARG, "unknown theta mode");
+    if (p->theta_mode != TEUK_THETA_CENTERED4 && p->theta_mode != TEUK_THETA_WENO5)
+        return fail(TEUK_ERR_ARG, "unknown theta mode");
     if (p->dt < 0.0 || !std::isfinite(p->dt)) return fail(TEUK_ERR_ARG, "dt must be >= 0");
     if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0))
         return fail(TEUK_ERR_ARG, "cfl must be in (0, 1] when dt == 0");
@@ -213,7 +214,7 @@ teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
 
 size_t teuk_coeff_count(const teuk_params* p) {
     if (teuk_check_params(p) != TEUK_OK) return 0;
-    return (size_t)kCoefPlanes * (size_t)p->nr * (size_t)p->ntheta;
+    return (size_t)coef_planes(p->theta_mode) * (size_t)p->nr * (size_t)p->ntheta;
 }
 
 teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coef) {
@@ -244,8 +245,10 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
             // fourth-order centred theta differences:
             //   12 dth^2 Psi_thth = -P(j+2) + 16 P(j+1) - 30 P(j) + 16 P(j-1) - P(j-2)
             //   12 dth   Psi_th   = -P(j+2) +  8 P(j+1)            -  8 P(j-1) + P(j-2)
+            const bool weno_th = p->theta_mode == TEUK_THETA_WENO5;
             const double A = dt * c.Ath / (12.0 * dth * dth);
-            const double B = dt * c.Bth / (12.0 * dth);
+            const double B = weno_th ? 0.0 : dt * c.Bth / (12.0 * dth);
+            if (weno_th) coef[kCBth * plane + q] = dt * c.Bth / (6.0 * dth);
             double w[5] = {-A + B, 16.0 * A - 8.0 * B, -30.0 * A + dt * c.Cr,
                            16.0 * A + 8.0 * B, -A - B};
             // Rows outside [0, nth) mirror across the pole with parity sigma:

@@ -6,15 +6,22 @@
 
 namespace teuk {
 
-// Number of coefficient planes the stage kernel reads per grid node.
+// Number of coefficient planes the stage kernel reads per grid node (one more
+// with the theta-WENO option: dt Bth / (6 dtheta)).
 constexpr int kCoefPlanes = 11;
+constexpr int kCoefPlanesThetaWeno = 12;
+inline int coef_planes(int theta_mode) {
+    return theta_mode == TEUK_THETA_WENO5 ? kCoefPlanesThetaWeno : kCoefPlanes;
+}
 // Plane order (all pre-multiplied by dt):
 //   0 cb   = b/(6h)          1 cKr = Re K/(6h)     2 cKi = Im K/(6h)
 //   3 cBr  = Re Bt           4 cBi = Im Bt         5 cCi = Im C
 //   6..10  theta stencil weights on Psi rows j-2, j-1, j, j+1, j+2
 //          (Ath and Bth centred differences, Re C on the centre, pole parity
 //          folded in).
-enum CoefPlane { kCb = 0, kCKr, kCKi, kCBr, kCBi, kCCi, kWm2, kWm1, kW0, kWp1, kWp2 };
+//   11     (theta-WENO option) dt Bth / (6 dtheta); the five stencil planes
+//          then hold only the second derivative and Re C.
+enum CoefPlane { kCb = 0, kCKr, kCKi, kCBr, kCBi, kCCi, kWm2, kWm1, kW0, kWp1, kWp2, kCBth };
 
 teuk_status fail(teuk_status st, const std::string& msg);
 void clear_error();
@@ -45,7 +52,7 @@ size_t batch_desc_bytes(int n);
 namespace teuk {
 cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_desc,
                               long long* items_out, cudaStream_t st);
-cudaError_t launch_batch_stage(int wprec, int stage, int segv, const void* d_desc, int n,
-                               long long items, int grid, cudaStream_t st);
+cudaError_t launch_batch_stage(int wprec, int theta, int stage, int segv, const void* d_desc,
+                               int n, long long items, int grid, cudaStream_t st);
 }  // namespace teuk
 #endif

@@ -69,6 +69,7 @@ struct StageArgs {
     int eps_pow2;         // eps is a power of two
     unsigned eps_mant;    // binary32 bits of eps 2^-eps_exp rounded to the
                           // weight format (a value in [1, 2])
+    unsigned pole_flip;   // 0x80000000 when the pole parity (-1)^(m+s) is odd
 };
 
 // ---------------------------------------------------------------------------
@@ -327,10 +328,30 @@ __device__ __forceinline__ double interface_flux(const double* sw, int idx, cons
     return __hiloint2double(hi, __double2loint(F));
 }
 
+// x with its sign bit XORed with mask (integer pipe).
+__device__ __forceinline__ double flip_sign(double x, unsigned mask) {
+    return __hiloint2double(__double2hiint(x) ^ (int)mask, __double2loint(x));
+}
+
+// 6 dtheta times the positive-direction WENO5 derivative at v[3] of the six
+// values v[0..5] (rows -3..+2 of the oriented theta line): the interfaces
+// +1/2 and -1/2 use the same first/third-difference flux form as in r*.
+template <int W>
+__device__ __forceinline__ double theta_weno_6hd(const double v[6], const StageArgs& A) {
+    const double d0 = v[1] - v[0], d1 = v[2] - v[1], d2 = v[3] - v[2];
+    const double d3 = v[4] - v[3], d4 = v[5] - v[4];
+    const double sa = fma(-2.0, d1, d0 + d2);
+    const double sb = fma(-2.0, d2, d1 + d3);
+    const double sc = fma(-2.0, d3, d2 + d4);
+    const double fp = flux6<W, false>(d1, d2, d3, d4, sb, sc, A);
+    const double fm = flux6<W, false>(d0, d1, d2, d3, sa, sb, A);
+    return fma(6.0, d2, fp) - fm;
+}
+
 // Right-hand side and Runge-Kutta combination at node i0 + p of row j
 // (Sec. 2.3, Sec. 3.2). sw holds the segment's first differences and flux
 // terms. Loads use a clamped node index; the caller stores only real nodes.
-template <int STAGE, class G>
+template <int W, int STAGE, int THETA, class G>
 __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw, int j,
                                             int i0, int p, double out[4]) {
     constexpr int NW = G::NW, FO = G::ND + G::NS;   // flux terms start at FO
@@ -379,6 +400,27 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
         acc2 = fma(w, __ldg(A.up + qq), acc2);
         acc3 = fma(w, __ldg(A.up + P + qq), acc3);
     }
+    if constexpr (THETA == TEUK_THETA_WENO5) {
+        // Bth dPsi/dtheta with the WENO5 theta derivative, upwinded by the
+        // sign of -Bth; the negative direction is the positive one on the
+        // mirrored line, negated. Rows beyond a pole reflect with parity.
+        const double cBt = __ldg(cf + kCBth * P);
+        const bool pos = !(cBt > 0.0);
+        double v0[6], v1[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            int jj = pos ? j + k - 3 : j + 3 - k;
+            unsigned flip = 0u;
+            if (jj < 0) { jj = -1 - jj; flip = A.pole_flip; }
+            if (jj >= A.nth) { jj = 2 * A.nth - 1 - jj; flip = A.pole_flip; }
+            const long long qq = (long long)jj * nr + i;
+            v0[k] = flip_sign(__ldg(A.up + qq), flip);
+            v1[k] = flip_sign(__ldg(A.up + P + qq), flip);
+        }
+        const double c = flip_sign(cBt, pos ? 0u : 0x80000000u);
+        acc2 = fma(c, theta_weno_6hd<W>(v0, A), acc2);
+        acc3 = fma(c, theta_weno_6hd<W>(v1, A), acc3);
+    }
     if (STAGE >= 2) {
         acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
         acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
@@ -390,7 +432,7 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
 
 // One warp's work: segment seg_blk (nodes seg_blk*SEG ..) of theta row j of
 // the evolution described by A. sw is the warp's shared-memory block.
-template <int W, int STAGE, int SEGV>
+template <int W, int STAGE, int THETA, int SEGV>
 __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, int lane, int j,
                                                 int seg_blk) {
     using G = Geo<SEGV>;
@@ -428,9 +470,9 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
     //    predicated)
     for (int p = lane; p < SEG; p += 64) {
         double ua[4], ub[4];
-        node_update<STAGE, G>(A, sw, j, i0, p, ua);
+        node_update<W, STAGE, THETA, G>(A, sw, j, i0, p, ua);
         const bool has_b = p + 32 < SEG;
-        if (has_b) node_update<STAGE, G>(A, sw, j, i0, p + 32, ub);
+        if (has_b) node_update<W, STAGE, THETA, G>(A, sw, j, i0, p + 32, ub);
         const long long P = A.plane;
         if (i0 + p < nr) {
             const long long q = row + i0 + p;
@@ -447,14 +489,14 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
 }
 
 // Single evolution: blockIdx.x = segment, blockIdx.y = block of WARPS rows.
-template <int W, int STAGE>
+template <int W, int STAGE, int THETA>
 __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     constexpr int SEGV = Seg<W>::value;
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
-    process_segment<W, STAGE, SEGV>(A, sm[warp], lane, j, blockIdx.x);
+    process_segment<W, STAGE, THETA, SEGV>(A, sm[warp], lane, j, blockIdx.x);
 }
 
 // Batched evolutions: one work item is a block of WARPS rows x one segment of
@@ -471,10 +513,10 @@ struct BatchDesc {
     long long item0;      // first work item of this evolution
     double dt, eps4;
     int eps_exp, eps_pow2;
-    unsigned eps_mant;
+    unsigned eps_mant, pole_flip;
 };
 
-template <int W, int STAGE, int SEGV>
+template <int W, int STAGE, int THETA, int SEGV>
 __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, int n,
                                                long long items) {
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
@@ -495,12 +537,13 @@ __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, 
             A.nr = d.nr; A.nth = d.nth; A.plane = d.plane;
             A.dt = d.dt; A.eps4 = d.eps4;
             A.eps_exp = d.eps_exp; A.eps_pow2 = d.eps_pow2; A.eps_mant = d.eps_mant;
+            A.pole_flip = d.pole_flip;
             double* w1 = d.w;
             double* w2 = d.w + 4 * d.plane;
             if (STAGE == 1) { A.un = nullptr; A.up = d.u; A.out = w1; A.alpha = 0.0; A.beta = 1.0; }
             if (STAGE == 2) { A.un = d.u; A.up = w1; A.out = w2; A.alpha = 0.75; A.beta = 0.25; }
             if (STAGE == 3) { A.un = d.u; A.up = w2; A.out = d.u; A.alpha = 1.0 / 3.0; A.beta = 2.0 / 3.0; }
-            process_segment<W, STAGE, SEGV>(A, sm[warp], lane, j, seg_blk);
+            process_segment<W, STAGE, THETA, SEGV>(A, sm[warp], lane, j, seg_blk);
         }
         __syncwarp();
     }
@@ -523,18 +566,28 @@ static void eps_parts(double eps, int wprec, int* E, int* pow2, unsigned* mant_b
     *mant_bits = (127u << 23) + (unsigned)(kept << (24 - P));
 }
 
-template <int W>
-static cudaError_t launch_stage_w(const StageArgs& A, int stage, cudaStream_t st) {
+template <int W, int THETA>
+static cudaError_t launch_stage_wt(const StageArgs& A, int stage, cudaStream_t st) {
     constexpr int SEG = Seg<W>::value;
     dim3 grid((A.nr + SEG - 1) / SEG, (A.nth + WARPS - 1) / WARPS);
     dim3 block(WARPS * 32);
     switch (stage) {
-    case 0: stage_kernel<W, 0><<<grid, block, 0, st>>>(A); break;
-    case 1: stage_kernel<W, 1><<<grid, block, 0, st>>>(A); break;
-    case 2: stage_kernel<W, 2><<<grid, block, 0, st>>>(A); break;
-    default: stage_kernel<W, 3><<<grid, block, 0, st>>>(A); break;
+    case 0: stage_kernel<W, 0, THETA><<<grid, block, 0, st>>>(A); break;
+    case 1: stage_kernel<W, 1, THETA><<<grid, block, 0, st>>>(A); break;
+    case 2: stage_kernel<W, 2, THETA><<<grid, block, 0, st>>>(A); break;
+    default: stage_kernel<W, 3, THETA><<<grid, block, 0, st>>>(A); break;
     }
     return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_stage_w(const StageArgs& A, int stage, int theta, cudaStream_t st) {
+    return theta == TEUK_THETA_WENO5 ? launch_stage_wt<W, TEUK_THETA_WENO5>(A, stage, st)
+                                     : launch_stage_wt<W, TEUK_THETA_CENTERED4>(A, stage, st);
+}
+
+static unsigned pole_flip_of(const teuk_params& p) {
+    return ((p.m + p.s) % 2 == 0) ? 0u : 0x80000000u;
 }
 
 cudaError_t launch_stage(const teuk_params& p, const double* coef, const double* un,
@@ -549,11 +602,13 @@ cudaError_t launch_stage(const teuk_params& p, const double* coef, const double*
     A.beta = stage == 2 ? 0.25 : (stage == 3 ? 2.0 / 3.0 : 1.0);
     A.eps4 = 4.0 * p.eps;
     eps_parts(p.eps, p.wprec, &A.eps_exp, &A.eps_pow2, &A.eps_mant);
+    A.pole_flip = pole_flip_of(p);
+    const int th = p.theta_mode;
     switch (p.wprec) {
-    case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, st);
-    case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, st);
-    case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, st);
-    default: return launch_stage_w<TEUK_W_BF16>(A, stage, st);
+    case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, th, st);
+    case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, th, st);
+    case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, th, st);
+    default: return launch_stage_w<TEUK_W_BF16>(A, stage, th, st);
     }
 }
 
@@ -578,6 +633,7 @@ cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_des
         d.item0 = item;
         d.dt = evos[k].dt; d.eps4 = 4.0 * p.eps;
         eps_parts(p.eps, p.wprec, &d.eps_exp, &d.eps_pow2, &d.eps_mant);
+        d.pole_flip = pole_flip_of(p);
         item += batch_items(p, segv);
     }
     *items_out = item;
@@ -589,33 +645,36 @@ cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_des
 
 size_t batch_desc_bytes(int n) { return sizeof(BatchDesc) * (size_t)n; }
 
-template <int W, int SEGV>
-static cudaError_t launch_batch_ws(int stage, const BatchDesc* d, int n, long long items,
-                                   int grid, cudaStream_t st) {
+template <int W, int THETA, int SEGV>
+static cudaError_t launch_batch_wts(int stage, const BatchDesc* d, int n, long long items,
+                                    int grid, cudaStream_t st) {
     const dim3 block(WARPS * 32);
     switch (stage) {
-    case 1: batch_stage_kernel<W, 1, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
-    case 2: batch_stage_kernel<W, 2, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
-    default: batch_stage_kernel<W, 3, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
+    case 1: batch_stage_kernel<W, 1, THETA, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
+    case 2: batch_stage_kernel<W, 2, THETA, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
+    default: batch_stage_kernel<W, 3, THETA, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
     }
     return cudaGetLastError();
 }
 
 template <int W>
-static cudaError_t launch_batch_w(int stage, int segv, const BatchDesc* d, int n, long long items,
-                                  int grid, cudaStream_t st) {
-    return segv == 64 ? launch_batch_ws<W, 64>(stage, d, n, items, grid, st)
-                      : launch_batch_ws<W, 32>(stage, d, n, items, grid, st);
+static cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, int n,
+                                  long long items, int grid, cudaStream_t st) {
+    if (theta == TEUK_THETA_WENO5)
+        return segv == 64 ? launch_batch_wts<W, TEUK_THETA_WENO5, 64>(stage, d, n, items, grid, st)
+                          : launch_batch_wts<W, TEUK_THETA_WENO5, 32>(stage, d, n, items, grid, st);
+    return segv == 64 ? launch_batch_wts<W, TEUK_THETA_CENTERED4, 64>(stage, d, n, items, grid, st)
+                      : launch_batch_wts<W, TEUK_THETA_CENTERED4, 32>(stage, d, n, items, grid, st);
 }
 
-cudaError_t launch_batch_stage(int wprec, int stage, int segv, const void* d_desc, int n,
-                               long long items, int grid, cudaStream_t st) {
+cudaError_t launch_batch_stage(int wprec, int theta, int stage, int segv, const void* d_desc,
+                               int n, long long items, int grid, cudaStream_t st) {
     const BatchDesc* d = static_cast<const BatchDesc*>(d_desc);
     switch (wprec) {
-    case TEUK_W_FP64: return launch_batch_w<TEUK_W_FP64>(stage, segv, d, n, items, grid, st);
-    case TEUK_W_FP32: return launch_batch_w<TEUK_W_FP32>(stage, segv, d, n, items, grid, st);
-    case TEUK_W_FP16: return launch_batch_w<TEUK_W_FP16>(stage, segv, d, n, items, grid, st);
-    default: return launch_batch_w<TEUK_W_BF16>(stage, segv, d, n, items, grid, st);
+    case TEUK_W_FP64: return launch_batch_w<TEUK_W_FP64>(stage, segv, theta, d, n, items, grid, st);
+    case TEUK_W_FP32: return launch_batch_w<TEUK_W_FP32>(stage, segv, theta, d, n, items, grid, st);
+    case TEUK_W_FP16: return launch_batch_w<TEUK_W_FP16>(stage, segv, theta, d, n, items, grid, st);
+    default: return launch_batch_w<TEUK_W_BF16>(stage, segv, theta, d, n, items, grid, st);
     }
 }
 

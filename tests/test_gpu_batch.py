@@ -56,6 +56,18 @@ def test_batch_members_equal_single_runs(wprec, autotune):
         np.testing.assert_array_equal(got, _single(w, ps[k], dt, 19))
 
 
+def test_batch_theta_weno_members_equal_single_runs():
+    ps = [T.params_from_workload(w, wprec="fp32", theta_mode=1) for w in MEMBERS]
+    b = T.teuk_batch_create(ps, autotune=True)
+    for k, w in enumerate(MEMBERS):
+        T.teuk_batch_set_state(b, k, I.initial_data(w), 0.0)
+    T.teuk_batch_step(b, 7)
+    for k, w in enumerate(MEMBERS):
+        dt, _, _, _ = T.teuk_batch_get_info(b, k)
+        got, _ = T.teuk_batch_get_state(b, k)
+        np.testing.assert_array_equal(got, _single(w, ps[k], dt, 7))
+
+
 def test_batch_member_matches_oracle():
     w = MEMBERS[4]
     ps = [T.params_from_workload(x, wprec="fp32") for x in MEMBERS]

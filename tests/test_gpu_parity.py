@@ -69,24 +69,25 @@ SHAPES = [(7, 5), (64, 8), (100, 13), (257, 33), (1000, 17)]
 PHYS = [(0.999, -2, 2), (0.0, 0, 0), (1.0, 0, 1), (0.5, -1, 0)]
 
 
+@pytest.mark.parametrize("theta_mode", [0, 1])
 @pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("phys", PHYS)
-def test_operator_parity(wprec, shape, phys):
+def test_operator_parity(wprec, shape, phys, theta_mode):
     nr, nth = shape
     a, s, m = phys
     rs0, rs1 = -40.0, 120.0
     seed = nr * 7 + nth
     for smooth in (True, False):
         u = multiscale_state(nr, nth, seed, smooth)
-        g = o.grid(nr, nth, rs0, rs1, 1.0, a, s, m, 1e-6, wprec)
+        g = o.grid(nr, nth, rs0, rs1, 1.0, a, s, m, 1e-6, wprec, theta_mode)
         F = o.rhs(g, o.coefficients(g), u)
-        p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m, wprec=wprec)
+        p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m, wprec=wprec, theta_mode=theta_mode)
         coef = dev(T.teuk_build_coefficients(p, 1.0))
         ud = dev(u)
         out = torch.empty_like(ud)
         T.teuk_stage_dev(p, 1.0, coef, None, ud, out, 0)
-        compare(host(out), F, what=f"{wprec} {shape} {phys} smooth={smooth}")
+        compare(host(out), F, what=f"{wprec} {shape} {phys} theta={theta_mode} smooth={smooth}")
 
 
 @pytest.mark.parametrize("wprec", ["fp64", "fp32"])
@@ -113,13 +114,21 @@ def test_rk_stages_parity(wprec):
     compare(host(una), exp_[3], tol=1e-13, what="stage 3 in place")
 
 
-def run_both(wl, wprec, nsteps, u0=None):
+@pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16"])
+def test_theta_weno_full_size_kerr(wprec):
+    """theta-WENO option on the 2048 x 128 Kerr workload: 2 steps, every node."""
+    got, exp_, ts = run_both(I.KERR_GRAV, wprec, 2, theta_mode=1)
+    compare(got, exp_, what=f"kerr theta-weno {wprec}", terms=ts)
+
+
+def run_both(wl, wprec, nsteps, u0=None, theta_mode=0):
     """nsteps of SSP-RK(3,3) on the GPU (stateless step) and in the oracle."""
-    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec)
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec,
+               theta_mode)
     co = o.coefficients(g)
     dt = oracle_dt(g, co)
     u0 = I.initial_data(wl) if u0 is None else u0
-    p = T.params_from_workload(wl, wprec=wprec)
+    p = T.params_from_workload(wl, wprec=wprec, theta_mode=theta_mode)
     coef = dev(T.teuk_build_coefficients(p, dt))
     ud = dev(u0)
     work = torch.empty(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")

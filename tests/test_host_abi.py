@@ -89,6 +89,18 @@ def test_coefficients_agree_with_oracle(a, s, m):
     np.testing.assert_allclose(acc, exp_, rtol=1e-8, atol=1e-10 * np.max(np.abs(exp_)))
 
 
+def test_theta_weno_option_adds_a_plane():
+    p = T.make_params(64, 16, a=0.5, s=-2, m=1, theta_mode=1)
+    assert T.teuk_check_params(p) == T.TEUK_OK
+    assert T.teuk_coeff_count(p) == 12 * 64 * 16
+    c1 = T.teuk_build_coefficients(p, 0.1)
+    p0 = T.make_params(64, 16, a=0.5, s=-2, m=1, theta_mode=0)
+    c0 = T.teuk_build_coefficients(p0, 0.1)
+    np.testing.assert_array_equal(c1[:6], c0[:6])
+    co = o.coefficients(o.grid(64, 16, -100.0, 300.0, 1.0, 0.5, -2, 1))
+    np.testing.assert_allclose(c1[11], 0.1 * co[8] / (6 * np.pi / 16), rtol=1e-9, atol=1e-15)
+
+
 def test_build_coefficients_rejects_bad_dt():
     p = T.make_params(64, 16)
     with pytest.raises(T.TeukError):

@@ -140,6 +140,28 @@ def test_theta_operator_on_spin_weighted_harmonics(case, a):
     assert errs[-1] < 1e-4 * abs(lam) + 1e-9
 
 
+@pytest.mark.parametrize("case", _eigen_cases())
+@pytest.mark.parametrize("a", [0.0, 0.6])
+def test_theta_weno_option_on_spin_weighted_harmonics(case, a):
+    """theta_mode 1 (WENO5 first theta derivative, reading): the discrete
+    operator still converges to the sY_lm eigenvalue relation (order > 3.3
+    over the last refinements once the weights have settled)."""
+    s, l, m, lam = case
+    errs = []
+    for nth in (64, 128, 256):
+        g = o.grid(16, nth, -10.0, 10.0, 1.0, a, s, m, 1e-6, "fp64", 1)
+        co = o.coefficients(g)
+        Y = I.swsh(s, l, m, I.theta_nodes(nth))
+        u = np.zeros((4, nth, 16))
+        u[0] = Y[:, None]
+        F = o.rhs(g, co, u)
+        res = F[2][:, 8] / co[7][:, 8] - lam * Y
+        errs.append(np.sqrt(np.mean(res ** 2)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders[-1] > 3.3, (errs, orders)
+    assert errs[-1] < 1e-5 * abs(lam) + 1e-9
+
+
 def test_assembly_matches_printed_real_matrices():
     """F = -(M du/dr* + L u + A u) with M, A, L exactly as printed in Sec. 2.3,
     using m31 = -Re K, m32 = Im K, a31 = -Re C, a32 = Im C, a33 = -Re Bt,
