@@ -122,11 +122,21 @@ class ClockSampler:
 
 
 def dist_init(gpus):
+    """Rank and world size from the torchrun environment; one process group
+    (NCCL on GPUs, gloo without) used only for the barrier and the max over
+    ranks of the timed region: the replicas exchange no data."""
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, world
+
+
+def weak_scaling_value(points_per_step, steps, world, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return points_per_step * steps * world / (max_ms * 1e-3)
 
 
 def max_over_ranks(x, world, device):
@@ -325,9 +335,8 @@ def main():
     batch = time_batch(T, torch, stream) if rank == 0 else None
 
     fp64_peak_tf = 2.0 * T.teuk_fp64_fma_rate(stream) / 1e12      # measured live
-    pts = POINTS * 3 * args.steps * world
-    value = pts / (ms32 * 1e-3)
-    value64 = pts / (ms64 * 1e-3)
+    value = weak_scaling_value(POINTS * 3, args.steps, world, ms32)
+    value64 = weak_scaling_value(POINTS * 3, args.steps, world, ms64)
     launch_ms = ms32 / (3 * args.steps)
     achieved_tf = FP64_FLOPS_PER_PT_STAGE * POINTS / (launch_ms * 1e-3) / 1e12
     achieved_gbs = BYTES_PER_PT_STAGE * POINTS / (launch_ms * 1e-3) / 1e9
