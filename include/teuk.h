@@ -65,6 +65,13 @@ typedef enum {
                                   stays fourth-order centred */
 } teuk_theta_mode;
 
+/* Time integrator (Sec. 3.2). */
+typedef enum {
+    TEUK_RK_SSP33 = 0,    /* SSP-RK(3,3), Shu-Osher form (the paper's choice)   */
+    TEUK_RK_SSP104 = 1    /* SSP-RK(10,4), ten forward-Euler stages of dt/6,
+                             low-storage (two-register) evaluation            */
+} teuk_rk;
+
 /* Problem statement (Sec. 2.1-2.3, Sec. 4): grid, domain, black hole, mode.
  * Valid ranges: nr >= 7, ntheta >= 5, rstar_max > rstar_min, M > 0,
  * 0 <= |a| <= M, s in {-2..2}, |m| <= 64, eps in [1e-60, 1],
@@ -79,6 +86,7 @@ typedef struct {
     double eps;                     /* WENO epsilon (Jiang-Shu use 1e-6)     */
     int wprec;                      /* teuk_wprec                            */
     int theta_mode;                 /* teuk_theta_mode                       */
+    int rk;                         /* teuk_rk                               */
 } teuk_params;
 
 typedef struct teuk_handle teuk_handle;
@@ -101,8 +109,10 @@ teuk_status teuk_check_params(const teuk_params* p);
  *   dt = cfl / max_ij [ b/h + sqrt(kappa) ],
  *   kappa = Ath (16/3)/dtheta^2 + |Bth| (3/2)/dtheta + |C|,
  * a bound of the largest frequency of the r* upwind part (b/h, Sec. 3.2
- * forward-Euler limit) plus the theta part of the second-order operator.
- * If p->dt > 0 it is returned unchanged. */
+ * forward-Euler limit) plus the theta part of the second-order operator;
+ * times 2.8 for TEUK_RK_SSP104 (the smaller of its real- and imaginary-axis
+ * stability extents relative to SSP-RK(3,3)). If p->dt > 0 it is returned
+ * unchanged. */
 teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out);
 
 /* Number of doubles in the kernel coefficient array of p (11 planes of
@@ -111,10 +121,11 @@ size_t teuk_coeff_count(const teuk_params* p);
 
 /* Kernel coefficient array for time step dt, written to host memory
  * coef_host[teuk_coeff_count(p)]. The planes are the first-order matrices
- * M, A, L of Sec. 2.3 pre-multiplied by dt (and 1/(6h), 1/(12 dtheta^k) for
- * the stencil normalisations), with the theta pole parity folded into the
- * five theta-stencil planes. Built on the host in binary64; r(r*) from the
- * tortoise relation of Sec. 2.2. */
+ * M, A, L of Sec. 2.3 pre-multiplied by the forward-Euler stage step of p's
+ * integrator (dt for SSP-RK(3,3), dt/6 for SSP-RK(10,4)) and by 1/(6h),
+ * 1/(12 dtheta^k) for the stencil normalisations, with the theta pole parity
+ * folded into the theta-stencil planes. Built on the host in binary64; r(r*)
+ * from the tortoise relation of Sec. 2.2. */
 teuk_status teuk_build_coefficients(const teuk_params* p, double dt,
                                     double* coef_host);
 
@@ -127,11 +138,12 @@ teuk_status teuk_fp64_fma_rate(void* stream, double* fma_per_s);
 
 /* ---- stateless device entry points (caller-owned device memory) --------- */
 
-/* One fused SSP-RK(3,3) stage (Sec. 3.2) on device arrays:
- *   stage 1: u_out = u_prev + dt F(u_prev)
- *   stage 2: u_out = 3/4 u_n + 1/4 (u_prev + dt F(u_prev))
- *   stage 3: u_out = 1/3 u_n + 2/3 (u_prev + dt F(u_prev))
- *   stage 0: u_out = dt F(u_prev)   (the operator alone, for checks)
+/* One fused Runge-Kutta stage (Sec. 3.2) on device arrays. With h the stage
+ * step of p's integrator (dt for SSP-RK(3,3), dt/6 for SSP-RK(10,4)):
+ *   stage 1: u_out = u_prev + h F(u_prev)
+ *   stage 2: u_out = 3/4 u_n + 1/4 (u_prev + h F(u_prev))   (SSP-RK(3,3) only)
+ *   stage 3: u_out = 1/3 u_n + 2/3 (u_prev + h F(u_prev))   (SSP-RK(3,3) only)
+ *   stage 0: u_out = h F(u_prev)    (the operator alone, for checks)
  * F is the right-hand side of Eq. evln with the WENO5 r* derivative.
  * dt must be the step coef_dev was built for (teuk_build_coefficients).
  * coef_dev: teuk_coeff_count(p) doubles. u_n (read for stages 2, 3; may be
@@ -143,10 +155,12 @@ teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_d
                            const double* u_n, const double* u_prev,
                            double* u_out, int stage, void* stream);
 
-/* nsteps full SSP-RK(3,3) steps (Sec. 3.2) in place on u_dev, using caller
- * scratch work_dev of 8*ntheta*nr doubles (the two intermediate stages).
- * dt, coef_dev as for teuk_stage_dev. Asynchronous on stream; u_dev holds
- * the state after the last step. work_dev must not overlap u_dev. */
+/* nsteps full steps of p's integrator (Sec. 3.2) in place on u_dev, using
+ * caller scratch work_dev of 8*ntheta*nr doubles for SSP-RK(3,3) (the two
+ * intermediate stages) or 12*ntheta*nr for SSP-RK(10,4) (two stage registers
+ * and the retained combination). dt, coef_dev as for teuk_stage_dev.
+ * Asynchronous on stream; u_dev holds the state after the last step.
+ * work_dev must not overlap u_dev. */
 teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_dev,
                           double* u_dev, double* work_dev, int64_t nsteps,
                           void* stream);
@@ -157,6 +171,7 @@ teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_de
  * direct cudaMalloc can fail or fragment the pool), and latency-critical loops
  * where cudaMalloc or cudaFree would synchronise the device. The paper has no
  * counterpart; this is a deployment convenience.
+ * SSP-RK(3,3) only (TEUK_ERR_ARG otherwise).
  * The two intermediate stage buffers live in a fixed array inside the library
  * (8 MiB, held by every GPU that loads the library until the process exits),
  * so ntheta*nr must be <= TEUK_STATIC_MAX_NODES; larger grids return
@@ -229,7 +244,7 @@ teuk_status teuk_state_dev(teuk_handle* h, double** u_dev);
  * teuk_stage_dev (Sec. 2.3, 3.1, 3.2) with its own coefficients and dt. */
 
 /* n members with parameters ps[0..n-1] (all with the same wprec and
- * theta_mode; dt == 0 takes each member's own stability rule). State starts at
+ * theta_mode, SSP-RK(3,3); dt == 0 takes each member's own stability rule). State starts at
  * zero, t = 0. autotune != 0 times the tile shapes (32- or 64-node segments)
  * and grid sizes (4 or 8 CTAs per SM) on a synthetic state and keeps the
  * fastest; otherwise the single-evolution defaults are used. stream as for

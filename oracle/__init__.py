@@ -61,6 +61,8 @@ def _load():
             "orc_rhs": (None, [P, P, P, P]),
             "orc_rk3_step": (None, [P, P, D, P, L]),
             "orc_rk3_linear": (None, [D, D, D, L, P]),
+            "orc_rk104_step": (None, [P, P, D, P, L]),
+            "orc_rk104_linear": (None, [D, D, D, L, P]),
             "orc_advect_1d": (None, [P, I, D, D, L, I, I, D]),
             "orc_observe": (None, [P, P, D, P, P]),
             "orc_num_threads": (I, []),
@@ -153,6 +155,19 @@ def rk3_step(g, coef, dt, u, nsteps=1):
     u = _f64(u).copy()
     _load().orc_rk3_step(ctypes.byref(g), _ptr(coef), dt, _ptr(u), int(nsteps))
     return u
+
+
+def rk104_step(g, coef, dt, u, nsteps=1):
+    coef = _f64(coef)
+    u = _f64(u).copy()
+    _load().orc_rk104_step(ctypes.byref(g), _ptr(coef), dt, _ptr(u), int(nsteps))
+    return u
+
+
+def rk104_linear(lam, dt, nsteps, y0=1.0 + 0.0j):
+    y = np.array([np.real(y0), np.imag(y0)], dtype=np.float64)
+    _load().orc_rk104_linear(float(np.real(lam)), float(np.imag(lam)), dt, int(nsteps), _ptr(y))
+    return complex(y[0], y[1])
 
 
 def rk3_linear(lam, dt, nsteps, y0=1.0 + 0.0j):

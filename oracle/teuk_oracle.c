@@ -458,6 +458,51 @@ void orc_rk3_step(const orc_grid* g, const double* coef, double dt, double* u,
     ssprk3(4L * g->nr * g->nth, u, dt, nsteps, pde_rhs, &c);
 }
 
+/* ------------------------------------------------------------------------ */
+/* SSP-RK(10,4), low-storage ten-stage fourth-order method as printed in     */
+/* Sec. 3.2 (Shu-Osher form):                                                */
+/*   u1 = u + dt/6 F(u); u_i = u_{i-1} + dt/6 F(u_{i-1}), i = 2..4;           */
+/*   u5 = 3/5 u + 2/5 u4 + dt/15 F(u4);                                      */
+/*   u_i = u_{i-1} + dt/6 F(u_{i-1}), i = 6..9;                              */
+/*   u^{n+1} = u/25 + 9/25 u4 + 3/5 u9 + 3/50 dt F(u4) + dt/10 F(u9).        */
+/* ------------------------------------------------------------------------ */
+static void ssprk104(long n, double* u, double dt, long nsteps, rhs_fn rhs,
+                     const void* ctx) {
+    double* ui = (double*)malloc(sizeof(double) * n);
+    double* u4 = (double*)malloc(sizeof(double) * n);
+    double* F4 = (double*)malloc(sizeof(double) * n);
+    double* Fv = (double*)malloc(sizeof(double) * n);
+    for (long step = 0; step < nsteps; ++step) {
+        memcpy(ui, u, sizeof(double) * n);
+        for (int i = 1; i <= 4; ++i) {
+            rhs(ctx, ui, Fv);
+            for (long k = 0; k < n; ++k) ui[k] = ui[k] + dt / 6.0 * Fv[k];
+        }
+        memcpy(u4, ui, sizeof(double) * n);
+        rhs(ctx, u4, F4);
+        for (long k = 0; k < n; ++k)
+            ui[k] = 3.0 / 5.0 * u[k] + 2.0 / 5.0 * u4[k] + dt / 15.0 * F4[k];
+        for (int i = 6; i <= 9; ++i) {
+            rhs(ctx, ui, Fv);
+            for (long k = 0; k < n; ++k) ui[k] = ui[k] + dt / 6.0 * Fv[k];
+        }
+        rhs(ctx, ui, Fv);
+        for (long k = 0; k < n; ++k)
+            u[k] = u[k] / 25.0 + 9.0 / 25.0 * u4[k] + 3.0 / 5.0 * ui[k]
+                 + 3.0 / 50.0 * dt * F4[k] + dt / 10.0 * Fv[k];
+    }
+    free(ui);
+    free(u4);
+    free(F4);
+    free(Fv);
+}
+
+void orc_rk104_step(const orc_grid* g, const double* coef, double dt, double* u,
+                    long nsteps) {
+    pde_ctx c = {g, coef};
+    ssprk104(4L * g->nr * g->nth, u, dt, nsteps, pde_rhs, &c);
+}
+
 typedef struct { double lr, li; } lin_ctx;
 
 static void lin_rhs(const void* ctx, const double* y, double* F) {
@@ -471,6 +516,12 @@ void orc_rk3_linear(double lam_re, double lam_im, double dt, long nsteps,
                     double y[2]) {
     lin_ctx c = {lam_re, lam_im};
     ssprk3(2, y, dt, nsteps, lin_rhs, &c);
+}
+
+void orc_rk104_linear(double lam_re, double lam_im, double dt, long nsteps,
+                      double y[2]) {
+    lin_ctx c = {lam_re, lam_im};
+    ssprk104(2, y, dt, nsteps, lin_rhs, &c);
 }
 
 typedef struct { int n, dir, wprec; double h, eps; } adv_ctx;

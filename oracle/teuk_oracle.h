@@ -53,6 +53,10 @@ void   orc_rk3_step(const orc_grid* g, const double* coef, double dt, double* u,
                     long nsteps);
 void   orc_rk3_linear(double lam_re, double lam_im, double dt, long nsteps,
                       double y[2]);
+void   orc_rk104_step(const orc_grid* g, const double* coef, double dt, double* u,
+                      long nsteps);
+void   orc_rk104_linear(double lam_re, double lam_im, double dt, long nsteps,
+                        double y[2]);
 void   orc_advect_1d(double* f, int n, double h, double dt, long nsteps, int dir,
                      int wprec, double eps);
 void   orc_observe(const orc_grid* g, const double* u, double rs_ext,

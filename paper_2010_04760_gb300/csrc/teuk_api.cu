@@ -16,6 +16,7 @@ namespace teuk {
 cudaError_t launch_stage(const teuk_params& p, const double* coef, const double* un,
                          const double* up, double* out, int stage, double dt,
                          cudaStream_t st);
+// launch_stage_ab, launch_rk104_combine: teuk_internal.h
 
 static teuk_status cuda_fail(cudaError_t e, const char* what) {
     return fail(TEUK_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -26,12 +27,47 @@ static teuk_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
     } while (0)
 
-// One SSP-RK(3,3) step: u -> w1 -> w2 -> u (Sec. 3.2).
+// State-sized scratch arrays one step of p's integrator needs.
+static int scratch_states(const teuk_params& p) { return p.rk == TEUK_RK_SSP104 ? 3 : 2; }
+
+// One step of p's integrator (Sec. 3.2) in place on u; w holds
+// scratch_states(p) arrays of 4 planes.
+//   SSP-RK(3,3): u -> w1 -> w2 -> u.
+//   SSP-RK(10,4): stages 1-5 are forward-Euler steps of dt/6 from u (A/B
+//   ping-pong), then q = u/25 + 9/25 u5' and u5 = 3/5 u + 2/5 u5' (u5' the fifth
+//   forward-Euler result), stages 6-9 forward Euler from u5, and
+//   u^{n+1} = q + 3/5 (u9 + dt/6 F(u9)): the printed Shu-Osher form rearranged
+//   into two registers plus q.
 static cudaError_t launch_step(const teuk_params& p, const double* coef, double dt,
-                               double* u, double* w1, double* w2, cudaStream_t st) {
-    cudaError_t e = launch_stage(p, coef, nullptr, u, w1, 1, dt, st);
-    if (e == cudaSuccess) e = launch_stage(p, coef, u, w1, w2, 2, dt, st);
-    if (e == cudaSuccess) e = launch_stage(p, coef, u, w2, u, 3, dt, st);
+                               double* u, double* w, cudaStream_t st) {
+    const size_t n = 4 * (size_t)p.nr * p.ntheta;
+    cudaError_t e = cudaSuccess;
+    if (p.rk == TEUK_RK_SSP104) {
+        const double h = dt / 6.0;
+        double* A = w;
+        double* B = w + n;
+        double* Q = w + 2 * n;
+        const double* src = u;
+        double* dst = A;
+        for (int i = 1; i <= 5 && e == cudaSuccess; ++i) {    // u1..u4, then u4 + h F(u4)
+            e = launch_stage_ab(p, coef, nullptr, src, dst, 1, h, 0.0, 1.0, st);
+            src = dst;
+            dst = (dst == A) ? B : A;
+        }
+        if (e == cudaSuccess) e = launch_rk104_combine(u, A, Q, B, (long long)n, st);  // B = u5
+        src = B;
+        dst = A;
+        for (int i = 6; i <= 9 && e == cudaSuccess; ++i) {    // u6..u9 (u9 in B)
+            e = launch_stage_ab(p, coef, nullptr, src, dst, 1, h, 0.0, 1.0, st);
+            src = dst;
+            dst = (dst == A) ? B : A;
+        }
+        if (e == cudaSuccess) e = launch_stage_ab(p, coef, Q, B, u, 2, h, 1.0, 3.0 / 5.0, st);
+        return e;
+    }
+    e = launch_stage(p, coef, nullptr, u, w, 1, dt, st);
+    if (e == cudaSuccess) e = launch_stage(p, coef, u, w, w + n, 2, dt, st);
+    if (e == cudaSuccess) e = launch_stage(p, coef, u, w + n, u, 3, dt, st);
     return e;
 }
 
@@ -128,6 +164,8 @@ teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_d
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
     if (stage < 0 || stage > 3) return fail(TEUK_ERR_ARG, "stage must be 0..3");
     if (!coef_dev || !u_prev || !u_out) return fail(TEUK_ERR_ARG, "NULL device pointer");
+    if (stage >= 2 && p->rk != TEUK_RK_SSP33)
+        return fail(TEUK_ERR_ARG, "stages 2 and 3 are SSP-RK(3,3) stages");
     if (stage >= 2 && !u_n) return fail(TEUK_ERR_ARG, "u_n is NULL for stage 2/3");
     if (u_out == u_prev) return fail(TEUK_ERR_ARG, "u_out aliases u_prev");
     TEUK_CUDA(launch_stage(*p, coef_dev, u_n, u_prev, u_out, stage, dt, (cudaStream_t)stream));
@@ -143,11 +181,10 @@ teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_de
     if (!coef_dev || !u_dev || !work_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
     if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
     const size_t n = 4 * (size_t)p->nr * p->ntheta;
-    if (work_dev < u_dev + n && u_dev < work_dev + 2 * n)
+    if (work_dev < u_dev + n && u_dev < work_dev + scratch_states(*p) * n)
         return fail(TEUK_ERR_ARG, "work_dev overlaps u_dev");
     for (int64_t k = 0; k < nsteps; ++k)
-        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, work_dev, work_dev + n,
-                              (cudaStream_t)stream));
+        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, work_dev, (cudaStream_t)stream));
     clear_error();
     return TEUK_OK;
 }
@@ -173,6 +210,8 @@ teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* 
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
     if (!coef_dev || !u_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
     if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+    if (p->rk != TEUK_RK_SSP33)
+        return fail(TEUK_ERR_ARG, "teuk_step_dev_static supports SSP-RK(3,3) only");
     int dev = 0;
     TEUK_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return fail(TEUK_ERR_ARG, "device ordinal out of range");
@@ -186,9 +225,8 @@ teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* 
         }
         stages = g_static_ptr[dev];
     }
-    const size_t n = 4 * nodes;
     for (int64_t k = 0; k < nsteps; ++k)
-        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, stages, stages + n, (cudaStream_t)stream));
+        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, stages, (cudaStream_t)stream));
     clear_error();
     return TEUK_OK;
 }
@@ -262,6 +300,8 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
         if (st != TEUK_OK) return fail(st, "member " + std::to_string(k) + ": " + teuk_last_error());
         if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode)
             return fail(TEUK_ERR_ARG, "all members need the same wprec and theta_mode");
+        if (ps[k].rk != TEUK_RK_SSP33)
+            return fail(TEUK_ERR_ARG, "batched evolutions use SSP-RK(3,3)");
     }
     teuk_batch* b = new teuk_batch();
     b->n = n;
@@ -440,7 +480,7 @@ teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
         h->own_stream = (e == cudaSuccess);
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->u, 4 * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->w, 8 * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->w, 4 * scratch_states(*p) * n * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->coef, coef.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->obs, 8 * (size_t)p->ntheta * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
@@ -504,14 +544,12 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
     if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
     if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
     const int kChunk = 16;
-    double* w1 = h->w;
-    double* w2 = h->w + 4 * h->plane();
     if (nsteps >= kChunk && !h->exec) {
         cudaGraph_t g = nullptr;
         TEUK_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < kChunk && e == cudaSuccess; ++k)
-            e = launch_step(h->p, h->coef, h->dt, h->u, w1, w2, h->stream);
+            e = launch_step(h->p, h->coef, h->dt, h->u, h->w, h->stream);
         cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
         if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
@@ -526,7 +564,7 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
         left -= h->chunk;
     }
     for (; left > 0; --left)
-        TEUK_CUDA(launch_step(h->p, h->coef, h->dt, h->u, w1, w2, h->stream));
+        TEUK_CUDA(launch_step(h->p, h->coef, h->dt, h->u, h->w, h->stream));
     h->t += (double)nsteps * h->dt;
     clear_error();
     return TEUK_OK;

@@ -178,6 +178,8 @@ teuk_status teuk_check_params(const teuk_params* p) {
         return fail(TEUK_ERR_ARG, "unknown weight precision");
     if (p->theta_mode != TEUK_THETA_CENTERED4 && p->theta_mode != TEUK_THETA_WENO5)
         return fail(TEUK_ERR_ARG, "unknown theta mode");
+    if (p->rk != TEUK_RK_SSP33 && p->rk != TEUK_RK_SSP104)
+        return fail(TEUK_ERR_ARG, "unknown time integrator");
     if (p->dt < 0.0 || !std::isfinite(p->dt)) return fail(TEUK_ERR_ARG, "dt must be >= 0");
     if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0))
         return fail(TEUK_ERR_ARG, "cfl must be in (0, 1] when dt == 0");
@@ -208,7 +210,9 @@ teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
     });
     double lam = 0.0;
     for (double v : row_lam) lam = std::fmax(lam, v);
-    *dt_out = p->cfl / lam;
+    // SSP-RK(10,4): 2.8 = min(4.92 / sqrt(3), 13.9 / 2.51), its imaginary- and
+    // real-axis stability extents relative to SSP-RK(3,3)
+    *dt_out = (p->rk == TEUK_RK_SSP104 ? 2.8 : 1.0) * p->cfl / lam;
     return TEUK_OK;
 }
 
@@ -227,6 +231,7 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
     const double h = (p->rstar_max - p->rstar_min) / (nr - 1);
     const double dth = M_PI / nth;
     const double sigma = ((p->m + p->s) % 2 == 0) ? 1.0 : -1.0;   // pole parity
+    dt = stage_step(*p, dt);                 // forward-Euler step of one stage
     const double c6h = dt / (6.0 * h);
     std::vector<double> r, x;
     radial_nodes(*p, r, x);

@@ -23,6 +23,12 @@ inline int coef_planes(int theta_mode) {
 //          then hold only the second derivative and Re C.
 enum CoefPlane { kCb = 0, kCKr, kCKi, kCBr, kCBi, kCCi, kWm2, kWm1, kW0, kWp1, kWp2, kCBth };
 
+// Forward-Euler step of one stage of p's integrator: dt for SSP-RK(3,3),
+// dt/6 for SSP-RK(10,4).
+inline double stage_step(const teuk_params& p, double dt) {
+    return p.rk == TEUK_RK_SSP104 ? dt / 6.0 : dt;
+}
+
 teuk_status fail(teuk_status st, const std::string& msg);
 void clear_error();
 
@@ -50,6 +56,11 @@ size_t batch_desc_bytes(int n);
 #ifdef __CUDACC__
 #include <cuda_runtime.h>
 namespace teuk {
+cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const double* un,
+                            const double* up, double* out, int kind, double h, double alpha,
+                            double beta, cudaStream_t st);
+cudaError_t launch_rk104_combine(const double* u, const double* v, double* q, double* u5,
+                                 long long n, cudaStream_t st);
 cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_desc,
                               long long* items_out, cudaStream_t st);
 cudaError_t launch_batch_stage(int wprec, int theta, int stage, int segv, const void* d_desc,

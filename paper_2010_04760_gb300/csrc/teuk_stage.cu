@@ -23,6 +23,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -593,13 +594,24 @@ static unsigned pole_flip_of(const teuk_params& p) {
 cudaError_t launch_stage(const teuk_params& p, const double* coef, const double* un,
                          const double* up, double* out, int stage, double dt,
                          cudaStream_t st) {
+    const double alpha = stage == 2 ? 0.75 : (stage == 3 ? 1.0 / 3.0 : 0.0);
+    const double beta = stage == 2 ? 0.25 : (stage == 3 ? 2.0 / 3.0 : 1.0);
+    return launch_stage_ab(p, coef, un, up, out, stage, stage_step(p, dt), alpha, beta, st);
+}
+
+// kind 0: u_out = h F(u_prev); kind 1: u_out = u_prev + h F(u_prev);
+// kind >= 2: u_out = alpha u_n + beta (u_prev + h F(u_prev)).
+cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const double* un,
+                            const double* up, double* out, int kind, double h, double alpha,
+                            double beta, cudaStream_t st) {
+    const int stage = kind > 2 ? 2 : kind;
     StageArgs A;
     A.coef = coef; A.un = un; A.up = up; A.out = out;
     A.nr = p.nr; A.nth = p.ntheta;
     A.plane = (long long)p.nr * p.ntheta;
-    A.dt = dt;
-    A.alpha = stage == 2 ? 0.75 : (stage == 3 ? 1.0 / 3.0 : 0.0);
-    A.beta = stage == 2 ? 0.25 : (stage == 3 ? 2.0 / 3.0 : 1.0);
+    A.dt = h;
+    A.alpha = alpha;
+    A.beta = beta;
     A.eps4 = 4.0 * p.eps;
     eps_parts(p.eps, p.wprec, &A.eps_exp, &A.eps_pow2, &A.eps_mant);
     A.pole_flip = pole_flip_of(p);
@@ -610,6 +622,30 @@ cudaError_t launch_stage(const teuk_params& p, const double* coef, const double*
     case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, th, st);
     default: return launch_stage_w<TEUK_W_BF16>(A, stage, th, st);
     }
+}
+
+// SSP-RK(10,4) after its fifth stage (v = u4 + dt/6 F(u4)), in the two-register
+// form: q = u/25 + 9/25 v (kept to the end of the step), u5 = 3/5 u + 2/5 v.
+__global__ void rk104_combine_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                     double* __restrict__ q, double* __restrict__ u5,
+                                     long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double uk = u[k], vk = v[k];
+        q[k] = fma(9.0 / 25.0, vk, uk / 25.0);
+        u5[k] = fma(2.0 / 5.0, vk, 3.0 / 5.0 * uk);
+    }
+}
+
+cudaError_t launch_rk104_combine(const double* u, const double* v, double* q, double* u5,
+                                 long long n, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((n + 255) / 256, (long long)sms * 8);
+    rk104_combine_kernel<<<(int)std::max<long long>(blocks, 1), 256, 0, st>>>(u, v, q, u5, n);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

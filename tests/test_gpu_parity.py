@@ -121,19 +121,54 @@ def test_theta_weno_full_size_kerr(wprec):
     compare(got, exp_, what=f"kerr theta-weno {wprec}", terms=ts)
 
 
-def run_both(wl, wprec, nsteps, u0=None, theta_mode=0):
+@pytest.mark.parametrize("wprec", ["fp64", "fp32"])
+def test_ssprk104_full_size_kerr(wprec):
+    """SSP-RK(10,4) (two-register evaluation on the GPU) against the oracle's
+    printed Shu-Osher form: 2048 x 128 Kerr workload, 2 steps, every node."""
+    got, exp_, ts = run_both(I.KERR_GRAV, wprec, 2, rk=1)
+    compare(got, exp_, what=f"kerr ssprk104 {wprec}", terms=ts)
+
+
+def test_ssprk104_handle_graph_matches_stateless():
+    wl = I.KERR_GRAV.with_(nr=300, nth=24)
+    p = T.params_from_workload(wl, wprec="fp32", rk=1)
+    h = T.teuk_create(p)
+    u0 = I.initial_data(wl)
+    T.teuk_set_state(h, u0, 0.0)
+    T.teuk_step(h, 19)
+    ref, t = T.teuk_get_state(h)
+    _, dt, _ = T.teuk_get_info(h)
+    coef = dev(T.teuk_build_coefficients(p, dt))
+    ud = dev(u0)
+    work = torch.empty(3, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    T.teuk_step_dev(p, dt, coef, ud, work, 19)
+    np.testing.assert_array_equal(host(ud), ref)
+    assert abs(t - 19 * dt) < 1e-12
+    assert abs(dt / T.teuk_stable_dt(T.params_from_workload(wl, wprec="fp32")) - 2.8) < 1e-12
+    with pytest.raises(T.TeukError):
+        T.teuk_stage_dev(p, dt, coef, ud, ud, torch.empty_like(ud), 2)
+    with pytest.raises(T.TeukError):
+        T.teuk_step_dev_static(p, dt, coef, ud, 1)
+    with pytest.raises(T.TeukError):
+        T.teuk_batch_create([p])
+
+
+def run_both(wl, wprec, nsteps, u0=None, theta_mode=0, rk=0):
     """nsteps of SSP-RK(3,3) on the GPU (stateless step) and in the oracle."""
     g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec,
                theta_mode)
     co = o.coefficients(g)
     dt = oracle_dt(g, co)
     u0 = I.initial_data(wl) if u0 is None else u0
-    p = T.params_from_workload(wl, wprec=wprec, theta_mode=theta_mode)
+    if rk == 1:
+        dt *= 2.8
+    p = T.params_from_workload(wl, wprec=wprec, theta_mode=theta_mode, rk=rk)
     coef = dev(T.teuk_build_coefficients(p, dt))
     ud = dev(u0)
-    work = torch.empty(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    work = torch.empty(3, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
     T.teuk_step_dev(p, dt, coef, ud, work, nsteps)
-    return host(ud), o.rk3_step(g, co, dt, u0, nsteps), term_scale(u0, dt, g, co)
+    step = o.rk104_step if rk == 1 else o.rk3_step
+    return host(ud), step(g, co, dt, u0, nsteps), term_scale(u0, dt, g, co)
 
 
 @pytest.mark.parametrize("wprec", ["fp64", "fp32"])

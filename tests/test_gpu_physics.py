@@ -98,3 +98,43 @@ def test_price_tail_on_gpu_matches_oracle():
         p = index(ts, ps)
         assert np.all(np.abs(p + 3.0) < 0.1), (wprec, p)
         assert np.max(np.abs(p - p_oracle)) < tol, (wprec, np.max(np.abs(p - p_oracle)))
+
+
+def test_price_tail_with_ssprk104():
+    """Sec. 3.2 reports no significant difference between SSP-RK(3,3) and
+    SSP-RK(10,4): with the ten-stage method (dt x 2.5) the GPU index p(t)
+    follows the oracle's SSP-RK(10,4) run and tends to -3."""
+    L, h, T_end = 400.0, 0.5, 650.0
+    nr, nth = int(round(2 * L / h)) + 1, 6
+    wl = I.Workload(name="tail", nr=nr, nth=nth, rs_min=-L, rs_max=L, rc=0.0, width=4.0,
+                    ells=(0,), seed=0)
+    dt = 2.5 * 0.4 * h
+    chunk = int(round(10.0 / dt))
+    nchunks = int(T_end / (chunk * dt))
+
+    def index(ts, ps):
+        ts, ps = np.array(ts), np.array(ps)
+        p = ts[1:-1] * (ps[2:] - ps[:-2]) / (ts[2:] - ts[:-2]) / ps[1:-1]
+        return p[ts[1:-1] > 250.0]
+
+    g = o.grid(nr, nth, -L, L, 1.0, 0.0, 0, 0, 1e-6, "fp64")
+    co = o.coefficients(g)
+    u = I.initial_data(wl)
+    ie = int(round((20.0 + L) / h))
+    ts, ps = [], []
+    for k in range(nchunks):
+        u = o.rk104_step(g, co, dt, u, chunk)
+        ts.append((k + 1) * chunk * dt)
+        ps.append(u[0, 0, ie])
+    p_oracle = index(ts, ps)
+    hd = T.teuk_create(T.params_from_workload(wl, wprec="fp64", dt=dt, rk=1))
+    T.teuk_set_state(hd, I.initial_data(wl), 0.0)
+    ts, ps = [], []
+    for _ in range(nchunks):
+        T.teuk_step(hd, chunk)
+        wv, _, t = T.teuk_observe(hd, 20.0)
+        ts.append(t)
+        ps.append(wv[0, 0])
+    p = index(ts, ps)
+    assert np.all(np.abs(p + 3.0) < 0.1), p
+    assert np.max(np.abs(p - p_oracle)) < 1e-8

@@ -101,6 +101,17 @@ def test_theta_weno_option_adds_a_plane():
     np.testing.assert_allclose(c1[11], 0.1 * co[8] / (6 * np.pi / 16), rtol=1e-9, atol=1e-15)
 
 
+def test_ssprk104_step_rule_and_stage_step():
+    p3 = T.make_params(128, 16, a=0.5, s=-2, m=2)
+    p10 = T.make_params(128, 16, a=0.5, s=-2, m=2, rk=1)
+    assert abs(T.teuk_stable_dt(p10) / T.teuk_stable_dt(p3) - 2.8) < 1e-12
+    # coefficients carry the forward-Euler stage step dt/6
+    np.testing.assert_allclose(T.teuk_build_coefficients(p10, 0.6),
+                               T.teuk_build_coefficients(p3, 0.1), rtol=1e-15, atol=0)
+    bad = T.make_params(128, 16, rk=2)
+    assert T.teuk_check_params(bad) == T.TEUK_ERR_ARG
+
+
 def test_build_coefficients_rejects_bad_dt():
     p = T.make_params(64, 16)
     with pytest.raises(T.TeukError):

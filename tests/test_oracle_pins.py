@@ -234,3 +234,54 @@ def test_ssprk33_third_order():
         errs.append(abs(o.rk3_linear(lam, 1.0 / ns, ns) - np.exp(lam)))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(orders - 3.0) < 0.15), orders
+
+
+# --------------------------------------------------------------------------
+# SSP coefficients stated in Sec. 3.2: C = 1 for SSP-RK(3,3), C = 6 for
+# SSP-RK(10,4). The one-step polynomial R(z) is recovered from the oracle's
+# integrators at roots of unity; C is the largest value for which R(-C + w)
+# has no negative Taylor coefficient in w (absolute monotonicity on [-C, 0]).
+# --------------------------------------------------------------------------
+def _stability_poly(step, degree, radius):
+    # sampled on a circle of the method's radius so that the small high-order
+    # coefficients are recovered with small relative error
+    n = 32
+    zs = radius * np.exp(2j * np.pi * np.arange(n) / n)
+    vals = np.array([step(z, 1.0, 1) for z in zs])
+    c = np.array([np.mean(vals * zs ** (-m)) for m in range(n)])
+    assert np.max(np.abs(c[degree + 1:]) * radius ** np.arange(degree + 1, n)) < 1e-10
+    return np.real(c[:degree + 1])
+
+
+def _shifted_coeffs(c, C):
+    """Coefficients of R(-C + w) in w, and the size of the terms summed for
+    each (the round-off scale of the expansion)."""
+    from math import comb
+    deg = len(c) - 1
+    val = np.array([sum(c[k] * comb(k, m) * (-C) ** (k - m) for k in range(m, deg + 1))
+                    for m in range(deg + 1)])
+    size = np.array([sum(abs(c[k]) * comb(k, m) * C ** (k - m) for k in range(m, deg + 1))
+                     for m in range(deg + 1)])
+    return val, size
+
+
+@pytest.mark.parametrize("step,degree,order,C", [(o.rk3_linear, 3, 3, 1.0),
+                                                 (o.rk104_linear, 10, 4, 6.0)])
+def test_ssp_coefficient_and_order(step, degree, order, C):
+    from math import factorial
+    c = _stability_poly(step, degree, C)
+    for k in range(order + 1):
+        assert abs(c[k] - 1.0 / factorial(k)) < 1e-12
+    if degree > order:                                   # exactly this order
+        assert abs(c[order + 1] - 1.0 / factorial(order + 1)) > 1e-5
+    val, size = _shifted_coeffs(c, C)
+    assert np.all(val >= -1e-12 * size), val
+    val, size = _shifted_coeffs(c, C * 1.02)
+    assert np.min(val + 1e-12 * size) < 0.0              # C is the threshold
+
+
+def test_ssprk104_fourth_order_convergence():
+    lam = -0.8 + 2.0j
+    errs = [abs(o.rk104_linear(lam, 1.0 / ns, ns) - np.exp(lam)) for ns in (10, 20, 40)]
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 4.0) < 0.2), orders
