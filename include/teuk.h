@@ -65,6 +65,16 @@ typedef enum {
                                   stays fourth-order centred */
 } teuk_theta_mode;
 
+/* Discretisation in r* (Sec. 3.1). */
+typedef enum {
+    TEUK_SCHEME_WENO5 = 0,    /* fifth-order WENO (Jiang-Shu), the method       */
+    TEUK_SCHEME_FD6_KO8 = 1   /* the paper's comparison scheme (Sec. 3.1.1):
+                                 sixth-order centred differences with the
+                                 Kreiss-Oliger term sigma h^7 D+^4 D-^4 / 256
+                                 subtracted from every component (the damping
+                                 sign); centred theta only, no weights       */
+} teuk_scheme;
+
 /* Time integrator (Sec. 3.2). */
 typedef enum {
     TEUK_RK_SSP33 = 0,    /* SSP-RK(3,3), Shu-Osher form (the paper's choice)   */
@@ -87,6 +97,8 @@ typedef struct {
     int wprec;                      /* teuk_wprec                            */
     int theta_mode;                 /* teuk_theta_mode                       */
     int rk;                         /* teuk_rk                               */
+    int scheme;                     /* teuk_scheme                           */
+    double ko_sigma;                /* Kreiss-Oliger sigma (paper: 0.01)     */
 } teuk_params;
 
 typedef struct teuk_handle teuk_handle;
@@ -244,7 +256,8 @@ teuk_status teuk_state_dev(teuk_handle* h, double** u_dev);
  * teuk_stage_dev (Sec. 2.3, 3.1, 3.2) with its own coefficients and dt. */
 
 /* n members with parameters ps[0..n-1] (all with the same wprec and
- * theta_mode, SSP-RK(3,3); dt == 0 takes each member's own stability rule). State starts at
+ * theta_mode, SSP-RK(3,3), WENO5; dt == 0 takes each member's own stability
+ * rule). State starts at
  * zero, t = 0. autotune != 0 times the tile shapes (32- or 64-node segments)
  * and grid sizes (4 or 8 CTAs per SM) on a synthetic state and keeps the
  * fastest; otherwise the single-evolution defaults are used. stream as for

@@ -40,7 +40,8 @@ class Grid(ctypes.Structure):
                 ("M", ctypes.c_double), ("a", ctypes.c_double),
                 ("s", ctypes.c_int), ("m", ctypes.c_int),
                 ("eps", ctypes.c_double), ("wprec", ctypes.c_int),
-                ("theta_mode", ctypes.c_int)]
+                ("theta_mode", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("ko_sigma", ctypes.c_double)]
 
 
 def _load():
@@ -58,6 +59,7 @@ def _load():
             "orc_weno5_weights": (None, [I, I, P, D, P]),
             "orc_weno5_flux": (D, [I, I, P, D, P, P, P]),
             "orc_weno5_deriv_1d": (None, [P, I, D, I, I, D, I, P, P, P, P]),
+            "orc_fd6_ko8_1d": (None, [P, I, D, D, I, P, P]),
             "orc_rhs": (None, [P, P, P, P]),
             "orc_rk3_step": (None, [P, P, D, P, L]),
             "orc_rk3_linear": (None, [D, D, D, L, P]),
@@ -83,9 +85,11 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def grid(nr, nth, rs_min, rs_max, M=1.0, a=0.0, s=0, m=0, eps=1e-6, wprec="fp64", theta_mode=0):
+def grid(nr, nth, rs_min, rs_max, M=1.0, a=0.0, s=0, m=0, eps=1e-6, wprec="fp64", theta_mode=0,
+         scheme=0, ko_sigma=0.01):
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
-    return Grid(nr, nth, rs_min, rs_max, M, a, s, m, eps, w, int(theta_mode))
+    return Grid(nr, nth, rs_min, rs_max, M, a, s, m, eps, w, int(theta_mode), int(scheme),
+                float(ko_sigma))
 
 
 def num_threads():
@@ -123,6 +127,13 @@ def weno5_weights(f5, dir, wprec="fp64", eps=1e-6):
     out = np.zeros(3)
     _load().orc_weno5_weights(w, dir, _ptr(f5), eps, _ptr(out))
     return out
+
+
+def fd6_ko8_1d(f, h, sigma=0.01, periodic=True):
+    f = _f64(f)
+    D, Q = np.zeros(f.size), np.zeros(f.size)
+    _load().orc_fd6_ko8_1d(_ptr(f), f.size, h, sigma, int(periodic), _ptr(D), _ptr(Q))
+    return D, Q
 
 
 def weno5_deriv_1d(f, h, dir, wprec="fp64", eps=1e-6, periodic=True, force_w=None,

@@ -27,6 +27,10 @@
  *    rounded; alpha normalised by the smallest (eps + IS). omega_0, omega_2
  *    promoted to binary64 and omega_1 = 1 - omega_0 - omega_2 there (Sec. 3.1.3).
  *  - WENO epsilon: a parameter (1e-6 by default), unstated in the paper.
+ *  - Comparison scheme (scheme 1, Sec. 3.1.1): the sixth-order centred r*
+ *    derivative for all four components and the Kreiss-Oliger term
+ *    sigma h^7 D+^4 D-^4 / 256 subtracted from every component's right-hand
+ *    side (the sign that damps), with edge-copy ghosts as for WENO.
  */
 #include <math.h>
 #include <complex.h>
@@ -325,6 +329,41 @@ void orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Comparison scheme of Sec. 3.1.1: the sixth-order centred derivative        */
+/*   D_j = (u_{j+3} - 9u_{j+2} + 45u_{j+1} - 45u_{j-1} + 9u_{j-2} - u_{j-3})     */
+/*         / (60 h)                                                          */
+/* and the Kreiss-Oliger operator Q = sigma h^7 D+^4 D-^4 / 256 with          */
+/* D+ u_j = (u_{j+1} - u_j)/h, D- u_j = (u_j - u_{j-1})/h, applied here       */
+/* literally (nested differences). Ghosts: periodic wrap or edge copies.      */
+/* ------------------------------------------------------------------------ */
+void orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int periodic,
+                    double* D, double* Q) {
+    const int G = 4;                                  /* ghost width */
+    int m = n + 2 * G;
+    double* a = (double*)malloc(sizeof(double) * m);
+    double* b = (double*)malloc(sizeof(double) * m);
+    for (int k = -G; k < n + G; ++k) {
+        int src = periodic ? ((k % n) + n) % n : (k < 0 ? 0 : (k >= n ? n - 1 : k));
+        a[k + G] = f[src];
+    }
+    for (int j = 0; j < n; ++j) {
+        const double* u = &a[j + G];
+        D[j] = (u[3] - 9.0 * u[2] + 45.0 * u[1] - 45.0 * u[-1] + 9.0 * u[-2] - u[-3])
+               / (60.0 * h);
+    }
+    /* D-^4 then D+^4 on the extended line (each application valid on a
+     * shrinking range; the centre j = 0..n-1 stays valid after all eight) */
+    memcpy(b, a, sizeof(double) * m);
+    for (int r = 0; r < 4; ++r)
+        for (int k = m - 1; k >= 1; --k) b[k] = (b[k] - b[k - 1]) / h;    /* D- */
+    for (int r = 0; r < 4; ++r)
+        for (int k = 0; k < m - 1; ++k) b[k] = (b[k + 1] - b[k]) / h;    /* D+ */
+    for (int j = 0; j < n; ++j) Q[j] = sigma * pow(h, 7) * b[j + G] / 256.0;
+    free(a);
+    free(b);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Right-hand side F(u) of du/dt = F(u) = -(M du/dr* + L u + A u)            */
 /* (Eq. evln). Psi components take the positive-direction WENO flux, pi      */
 /* components the negative-direction one, by the sign of M's diagonal        */
@@ -343,10 +382,16 @@ void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) 
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < nth; ++j) {
         double* Dc = (double*)malloc(sizeof(double) * 4 * nr);
+        double* Qc = (double*)calloc(4 * (size_t)nr, sizeof(double));
         for (int c = 0; c < 4; ++c) {
-            int dir = (c < 2) ? +1 : -1;
-            orc_weno5_deriv_1d(&u[c * plane + (long)j * nr], nr, h, dir, g->wprec,
-                               g->eps, 0, NULL, &Dc[c * nr], NULL, NULL);
+            if (g->scheme == 1) {
+                orc_fd6_ko8_1d(&u[c * plane + (long)j * nr], nr, h, g->ko_sigma, 0,
+                               &Dc[c * nr], &Qc[c * nr]);
+            } else {
+                int dir = (c < 2) ? +1 : -1;
+                orc_weno5_deriv_1d(&u[c * plane + (long)j * nr], nr, h, dir, g->wprec,
+                                   g->eps, 0, NULL, &Dc[c * nr], NULL, NULL);
+            }
         }
         /* rows j-2 .. j+2 of Psi, with ghosts across the poles */
         int rows[5];
@@ -408,12 +453,14 @@ void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) 
             double complex Fpsi = pi - b * Dpsi;
             double complex Fpi = b * Dpi + K * Dpsi + Ath * psi_thth
                                  + Bth * psi_th + Bt * pi + C * psi;
-            F[0 * plane + p] = creal(Fpsi);
-            F[1 * plane + p] = cimag(Fpsi);
-            F[2 * plane + p] = creal(Fpi);
-            F[3 * plane + p] = cimag(Fpi);
+            /* scheme 1: the Kreiss-Oliger term is subtracted (dissipative sign) */
+            F[0 * plane + p] = creal(Fpsi) - Qc[0 * nr + i];
+            F[1 * plane + p] = cimag(Fpsi) - Qc[1 * nr + i];
+            F[2 * plane + p] = creal(Fpi) - Qc[2 * nr + i];
+            F[3 * plane + p] = cimag(Fpi) - Qc[3 * nr + i];
         }
         free(Dc);
+        free(Qc);
     }
 }
 

@@ -33,6 +33,8 @@ typedef struct {
     double eps;              /* WENO epsilon                                     */
     int wprec;               /* weight precision code                            */
     int theta_mode;          /* 0: centred dtheta; 1: WENO5 dtheta (reading)     */
+    int scheme;              /* 0: WENO5 in r*; 1: FD6 + KO8 (Sec. 3.1.1)        */
+    double ko_sigma;         /* Kreiss-Oliger sigma of scheme 1                  */
 } orc_grid;
 
 double orc_rstar_of_r(double r, double M, double a);
@@ -45,6 +47,8 @@ void   orc_weno5_weights(int wprec, int dir, const double* f5, double eps,
                          double w[3]);
 double orc_weno5_flux(int wprec, int dir, const double* f5, double eps,
                       const double* force_w, double w_out[3], double q_out[3]);
+void   orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int periodic,
+                      double* D, double* Q);
 void   orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
                           double eps, int periodic, const double* force_w,
                           double* D, double* w_out, double* q_out);

@@ -22,6 +22,7 @@ TEUK_OK, TEUK_ERR_ARG, TEUK_ERR_CUDA, TEUK_ERR_NONFINITE, TEUK_ERR_TIMEOUT, TEUK
 TEUK_W_FP64, TEUK_W_FP32, TEUK_W_FP16, TEUK_W_BF16 = range(4)
 TEUK_THETA_CENTERED4, TEUK_THETA_WENO5 = 0, 1
 TEUK_RK_SSP33, TEUK_RK_SSP104 = 0, 1
+TEUK_SCHEME_WENO5, TEUK_SCHEME_FD6_KO8 = 0, 1
 WPREC = {"fp64": TEUK_W_FP64, "fp32": TEUK_W_FP32, "fp16": TEUK_W_FP16, "bf16": TEUK_W_BF16}
 COEF_PLANES = 11
 
@@ -39,7 +40,8 @@ class teuk_params(ctypes.Structure):
                 ("s", ctypes.c_int), ("m", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("eps", ctypes.c_double), ("wprec", ctypes.c_int),
-                ("theta_mode", ctypes.c_int), ("rk", ctypes.c_int)]
+                ("theta_mode", ctypes.c_int), ("rk", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("ko_sigma", ctypes.c_double)]
 
 
 _lib = None
@@ -134,10 +136,10 @@ def _host(a):
 
 def make_params(nr, ntheta, rstar_min=-100.0, rstar_max=300.0, M=1.0, a=0.0, s=0, m=0,
                 cfl=0.5, dt=0.0, eps=1e-6, wprec="fp64", theta_mode=TEUK_THETA_CENTERED4,
-                rk=TEUK_RK_SSP33):
+                rk=TEUK_RK_SSP33, scheme=TEUK_SCHEME_WENO5, ko_sigma=0.01):
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
     return teuk_params(nr, ntheta, rstar_min, rstar_max, M, a, s, m, cfl, dt, eps, w, theta_mode,
-                       rk)
+                       rk, scheme, ko_sigma)
 
 
 def params_from_workload(wl, **over):

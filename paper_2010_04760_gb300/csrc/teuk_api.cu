@@ -300,8 +300,8 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
         if (st != TEUK_OK) return fail(st, "member " + std::to_string(k) + ": " + teuk_last_error());
         if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode)
             return fail(TEUK_ERR_ARG, "all members need the same wprec and theta_mode");
-        if (ps[k].rk != TEUK_RK_SSP33)
-            return fail(TEUK_ERR_ARG, "batched evolutions use SSP-RK(3,3)");
+        if (ps[k].rk != TEUK_RK_SSP33 || ps[k].scheme != TEUK_SCHEME_WENO5)
+            return fail(TEUK_ERR_ARG, "batched evolutions use WENO5 and SSP-RK(3,3)");
     }
     teuk_batch* b = new teuk_batch();
     b->n = n;

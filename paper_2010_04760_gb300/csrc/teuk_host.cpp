@@ -180,6 +180,12 @@ teuk_status teuk_check_params(const teuk_params* p) {
         return fail(TEUK_ERR_ARG, "unknown theta mode");
     if (p->rk != TEUK_RK_SSP33 && p->rk != TEUK_RK_SSP104)
         return fail(TEUK_ERR_ARG, "unknown time integrator");
+    if (p->scheme != TEUK_SCHEME_WENO5 && p->scheme != TEUK_SCHEME_FD6_KO8)
+        return fail(TEUK_ERR_ARG, "unknown r* scheme");
+    if (p->scheme == TEUK_SCHEME_FD6_KO8 && p->theta_mode != TEUK_THETA_CENTERED4)
+        return fail(TEUK_ERR_ARG, "the FD6+KO8 scheme uses centred theta differences");
+    if (p->scheme == TEUK_SCHEME_FD6_KO8 && !(p->ko_sigma >= 0.0 && p->ko_sigma <= 1.0))
+        return fail(TEUK_ERR_ARG, "ko_sigma must be in [0, 1]");
     if (p->dt < 0.0 || !std::isfinite(p->dt)) return fail(TEUK_ERR_ARG, "dt must be >= 0");
     if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0))
         return fail(TEUK_ERR_ARG, "cfl must be in (0, 1] when dt == 0");

@@ -25,6 +25,7 @@
 #include <cstdint>
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "teuk_internal.h"
@@ -55,6 +56,11 @@ template <int W> struct Seg {
 template <int S> struct Geo {
     static constexpr int SEG = S, ND = S + 5, NS = S + 3, NF = S + 1, NW = ND + NS + NF;
 };
+// The FD6 + KO8 comparison scheme needs only first differences, with a
+// 4-node halo (k = i0-4 .. i0+S+3).
+template <int S> struct GeoFD {
+    static constexpr int SEG = S, ND = S + 8, NS = 0, NF = 0, NW = ND;
+};
 
 struct StageArgs {
     const double* coef;   // kCoefPlanes planes of nth*nr
@@ -71,6 +77,7 @@ struct StageArgs {
     unsigned eps_mant;    // binary32 bits of eps 2^-eps_exp rounded to the
                           // weight format (a value in [1, 2])
     unsigned pole_flip;   // 0x80000000 when the pole parity (-1)^(m+s) is odd
+    double ko;            // FD6+KO8 scheme: h_stage sigma / (256 h), else 0
 };
 
 // ---------------------------------------------------------------------------
@@ -352,7 +359,19 @@ __device__ __forceinline__ double theta_weno_6hd(const double v[6], const StageA
 // Right-hand side and Runge-Kutta combination at node i0 + p of row j
 // (Sec. 2.3, Sec. 3.2). sw holds the segment's first differences and flux
 // terms. Loads use a clamped node index; the caller stores only real nodes.
-template <int W, int STAGE, int THETA, class G>
+// 6h times the sixth-order centred derivative and the eighth difference
+// delta^8 u at a node, from the first differences d[-4..3] around it
+// (d[m] = u_{j+m+1} - u_{j+m}):
+//   60 h u' = (d-3 + d2) - 8 (d-2 + d1) + 37 (d-1 + d0)     (Sec. 3.1.1 stencil)
+//   delta^8 u = (d3 - d-4) + 7 (d-3 - d2) + 21 (d1 - d-2) + 35 (d-1 - d0).
+__device__ __forceinline__ void fd6_ko8(const double* d, double& D6h, double& e8) {
+    const double t = fma(-8.0, d[2] + d[5], d[1] + d[6]);
+    D6h = 0.1 * fma(37.0, d[3] + d[4], t);
+    const double u = fma(7.0, d[1] - d[6], d[7] - d[0]);
+    e8 = fma(35.0, d[3] - d[4], fma(21.0, d[5] - d[2], u));
+}
+
+template <int W, int STAGE, int THETA, class G, int SCHEME = 0>
 __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw, int j,
                                             int i0, int p, double out[4]) {
     constexpr int NW = G::NW, FO = G::ND + G::NS;   // flux terms start at FO
@@ -361,11 +380,19 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     const long long P = A.plane;
     const long long q = (long long)j * nr + i;
     const double* cf = A.coef + q;
-    // 6 h D for each component
-    const double D0 = fma(6.0, sw[0 * NW + p + 2], sw[0 * NW + FO + p + 1]) - sw[0 * NW + FO + p];
-    const double D1 = fma(6.0, sw[1 * NW + p + 2], sw[1 * NW + FO + p + 1]) - sw[1 * NW + FO + p];
-    const double D2 = fma(6.0, sw[2 * NW + p + 3], sw[2 * NW + FO + p + 1]) - sw[2 * NW + FO + p];
-    const double D3 = fma(6.0, sw[3 * NW + p + 3], sw[3 * NW + FO + p + 1]) - sw[3 * NW + FO + p];
+    // 6 h D for each component (and the eighth differences of the FD6+KO8 scheme)
+    double D0, D1, D2, D3, E0 = 0.0, E1 = 0.0, E2 = 0.0, E3 = 0.0;
+    if constexpr (SCHEME == 1) {
+        fd6_ko8(sw + 0 * NW + p, D0, E0);
+        fd6_ko8(sw + 1 * NW + p, D1, E1);
+        fd6_ko8(sw + 2 * NW + p, D2, E2);
+        fd6_ko8(sw + 3 * NW + p, D3, E3);
+    } else {
+        D0 = fma(6.0, sw[0 * NW + p + 2], sw[0 * NW + FO + p + 1]) - sw[0 * NW + FO + p];
+        D1 = fma(6.0, sw[1 * NW + p + 2], sw[1 * NW + FO + p + 1]) - sw[1 * NW + FO + p];
+        D2 = fma(6.0, sw[2 * NW + p + 3], sw[2 * NW + FO + p + 1]) - sw[2 * NW + FO + p];
+        D3 = fma(6.0, sw[3 * NW + p + 3], sw[3 * NW + FO + p + 1]) - sw[3 * NW + FO + p];
+    }
     const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
     const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
     const double cb = __ldg(cf + kCb * P), cKr = __ldg(cf + kCKr * P);
@@ -422,6 +449,12 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
         acc2 = fma(c, theta_weno_6hd<W>(v0, A), acc2);
         acc3 = fma(c, theta_weno_6hd<W>(v1, A), acc3);
     }
+    if constexpr (SCHEME == 1) {    // Kreiss-Oliger dissipation, subtracted
+        acc0 = fma(-A.ko, E0, acc0);
+        acc1 = fma(-A.ko, E1, acc1);
+        acc2 = fma(-A.ko, E2, acc2);
+        acc3 = fma(-A.ko, E3, acc3);
+    }
     if (STAGE >= 2) {
         acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
         acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
@@ -433,11 +466,12 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
 
 // One warp's work: segment seg_blk (nodes seg_blk*SEG ..) of theta row j of
 // the evolution described by A. sw is the warp's shared-memory block.
-template <int W, int STAGE, int THETA, int SEGV>
+template <int W, int STAGE, int THETA, int SEGV, int SCHEME = 0>
 __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, int lane, int j,
                                                 int seg_blk) {
-    using G = Geo<SEGV>;
+    using G = std::conditional_t<SCHEME == 1, GeoFD<SEGV>, Geo<SEGV>>;
     constexpr int SEG = G::SEG, ND = G::ND, NS = G::NS, NF = G::NF, NW = G::NW;
+    constexpr int HALO = SCHEME == 1 ? 4 : 3;
     const int nr = A.nr;
     const int i0 = seg_blk * SEG;
     const long long row = (long long)j * nr;
@@ -445,15 +479,16 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
 #define SD(c, k) sw[(c) * NW + ND + (k)]
 #define FL(c, k) sw[(c) * NW + ND + NS + (k)]
 
-    // 1. first differences d_k, k = i0-3 .. i0+SEG+1 (edge ghosts: d = 0)
+    // 1. first differences d_k, k = i0-HALO .. (edge ghosts: d = 0)
     for (int idx = lane; idx < 4 * ND; idx += 32) {
         const int c = idx / ND, k = idx - c * ND;
-        const int g = i0 - 3 + k;
+        const int g = i0 - HALO + k;
         const double* f = A.up + c * A.plane + row;
         const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
         DL(c, k) = __ldg(f + ib) - __ldg(f + ia);
     }
     __syncwarp();
+    if constexpr (SCHEME == 0) {
     // 2. s_k = d_{k-1} - 2 d_k + d_{k+1}, k = i0-2 .. i0+SEG
     for (int idx = lane; idx < 4 * NS; idx += 32) {
         const int c = idx / NS, k = idx - c * NS;
@@ -466,14 +501,15 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
         FL(c, idx - c * NF) = interface_flux<W, G>(sw, idx, A);
     }
     __syncwarp();
+    }
     // 4. nodes i = i0 .. i0+SEG-1 (two per lane and iteration, computed side
     //    by side; the second node's loads use a clamped index and its store is
     //    predicated)
     for (int p = lane; p < SEG; p += 64) {
         double ua[4], ub[4];
-        node_update<W, STAGE, THETA, G>(A, sw, j, i0, p, ua);
+        node_update<W, STAGE, THETA, G, SCHEME>(A, sw, j, i0, p, ua);
         const bool has_b = p + 32 < SEG;
-        if (has_b) node_update<W, STAGE, THETA, G>(A, sw, j, i0, p + 32, ub);
+        if (has_b) node_update<W, STAGE, THETA, G, SCHEME>(A, sw, j, i0, p + 32, ub);
         const long long P = A.plane;
         if (i0 + p < nr) {
             const long long q = row + i0 + p;
@@ -498,6 +534,18 @@ __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
     process_segment<W, STAGE, THETA, SEGV>(A, sm[warp], lane, j, blockIdx.x);
+}
+
+// FD6 + KO8 comparison scheme (Sec. 3.1.1), single evolution, centred theta.
+template <int STAGE>
+__global__ void TEUK_BOUNDS fd6_stage_kernel(const StageArgs A) {
+    constexpr int SEGV = 32;
+    __shared__ double sm[WARPS][4 * GeoFD<SEGV>::NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.y * WARPS + warp;
+    if (j >= A.nth) return;
+    process_segment<TEUK_W_FP64, STAGE, TEUK_THETA_CENTERED4, SEGV, 1>(A, sm[warp], lane, j,
+                                                                      blockIdx.x);
 }
 
 // Batched evolutions: one work item is a block of WARPS rows x one segment of
@@ -539,6 +587,7 @@ __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, 
             A.dt = d.dt; A.eps4 = d.eps4;
             A.eps_exp = d.eps_exp; A.eps_pow2 = d.eps_pow2; A.eps_mant = d.eps_mant;
             A.pole_flip = d.pole_flip;
+            A.ko = 0.0;
             double* w1 = d.w;
             double* w2 = d.w + 4 * d.plane;
             if (STAGE == 1) { A.un = nullptr; A.up = d.u; A.out = w1; A.alpha = 0.0; A.beta = 1.0; }
@@ -615,6 +664,17 @@ cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const doub
     A.eps4 = 4.0 * p.eps;
     eps_parts(p.eps, p.wprec, &A.eps_exp, &A.eps_pow2, &A.eps_mant);
     A.pole_flip = pole_flip_of(p);
+    A.ko = 0.0;
+    if (p.scheme == TEUK_SCHEME_FD6_KO8) {
+        A.ko = h * p.ko_sigma / (256.0 * ((p.rstar_max - p.rstar_min) / (p.nr - 1)));
+        dim3 grid((A.nr + 31) / 32, (A.nth + WARPS - 1) / WARPS), block(WARPS * 32);
+        switch (stage) {
+        case 0: fd6_stage_kernel<0><<<grid, block, 0, st>>>(A); break;
+        case 1: fd6_stage_kernel<1><<<grid, block, 0, st>>>(A); break;
+        default: fd6_stage_kernel<2><<<grid, block, 0, st>>>(A); break;
+        }
+        return cudaGetLastError();
+    }
     const int th = p.theta_mode;
     switch (p.wprec) {
     case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, th, st);

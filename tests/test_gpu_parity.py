@@ -121,6 +121,32 @@ def test_theta_weno_full_size_kerr(wprec):
     compare(got, exp_, what=f"kerr theta-weno {wprec}", terms=ts)
 
 
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("phys", PHYS)
+def test_fd6_ko8_operator_parity(shape, phys):
+    """The comparison scheme (Sec. 3.1.1): FD6 derivative and KO8 dissipation."""
+    nr, nth = shape
+    a, s, m = phys
+    rs0, rs1 = -40.0, 120.0
+    for smooth in (True, False):
+        u = multiscale_state(nr, nth, nr * 3 + nth, smooth)
+        g = o.grid(nr, nth, rs0, rs1, 1.0, a, s, m, scheme=1, ko_sigma=0.2)
+        co = o.coefficients(g)
+        F = o.rhs(g, co, u)
+        p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m, scheme=1, ko_sigma=0.2)
+        coef = dev(T.teuk_build_coefficients(p, 1.0))
+        ud = dev(u)
+        out = torch.empty_like(ud)
+        T.teuk_stage_dev(p, 1.0, coef, None, ud, out, 0)
+        compare(host(out), F, what=f"fd6 {shape} {phys} smooth={smooth}",
+                terms=term_scale(u, 1.0, g, co))
+
+
+def test_fd6_ko8_full_size_kerr():
+    got, exp_, ts = run_both(I.KERR_GRAV, "fp64", 3, scheme=1)
+    compare(got, exp_, what="kerr fd6", terms=ts)
+
+
 @pytest.mark.parametrize("wprec", ["fp64", "fp32"])
 def test_ssprk104_full_size_kerr(wprec):
     """SSP-RK(10,4) (two-register evaluation on the GPU) against the oracle's
@@ -153,16 +179,16 @@ def test_ssprk104_handle_graph_matches_stateless():
         T.teuk_batch_create([p])
 
 
-def run_both(wl, wprec, nsteps, u0=None, theta_mode=0, rk=0):
-    """nsteps of SSP-RK(3,3) on the GPU (stateless step) and in the oracle."""
+def run_both(wl, wprec, nsteps, u0=None, theta_mode=0, rk=0, scheme=0):
+    """nsteps on the GPU (stateless step) and in the oracle."""
     g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec,
-               theta_mode)
+               theta_mode, scheme=scheme)
     co = o.coefficients(g)
     dt = oracle_dt(g, co)
     u0 = I.initial_data(wl) if u0 is None else u0
     if rk == 1:
         dt *= 2.8
-    p = T.params_from_workload(wl, wprec=wprec, theta_mode=theta_mode, rk=rk)
+    p = T.params_from_workload(wl, wprec=wprec, theta_mode=theta_mode, rk=rk, scheme=scheme)
     coef = dev(T.teuk_build_coefficients(p, dt))
     ud = dev(u0)
     work = torch.empty(3, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")

@@ -112,6 +112,13 @@ def test_ssprk104_step_rule_and_stage_step():
     assert T.teuk_check_params(bad) == T.TEUK_ERR_ARG
 
 
+def test_fd6_scheme_argument_rules():
+    assert T.teuk_check_params(T.make_params(64, 16, scheme=1)) == T.TEUK_OK
+    assert T.teuk_check_params(T.make_params(64, 16, scheme=2)) == T.TEUK_ERR_ARG
+    assert T.teuk_check_params(T.make_params(64, 16, scheme=1, theta_mode=1)) == T.TEUK_ERR_ARG
+    assert T.teuk_check_params(T.make_params(64, 16, scheme=1, ko_sigma=-0.1)) == T.TEUK_ERR_ARG
+
+
 def test_build_coefficients_rejects_bad_dt():
     p = T.make_params(64, 16)
     with pytest.raises(T.TeukError):

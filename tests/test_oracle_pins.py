@@ -285,3 +285,43 @@ def test_ssprk104_fourth_order_convergence():
     errs = [abs(o.rk104_linear(lam, 1.0 / ns, ns) - np.exp(lam)) for ns in (10, 20, 40)]
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(orders - 4.0) < 0.2), orders
+
+
+# --------------------------------------------------------------------------
+# FD6 + KO8 comparison scheme (Sec. 3.1.1)
+# --------------------------------------------------------------------------
+def test_fd6_exact_to_degree_six_and_sixth_order():
+    n, h = 48, 0.1
+    x = np.arange(n) * h
+    for deg in range(7):
+        f = (x - 2.1) ** deg
+        D, _ = o.fd6_ko8_1d(f, h, 0.01, periodic=False)
+        ex = deg * (x - 2.1) ** (deg - 1) if deg else 0 * x
+        assert np.max(np.abs(D[5:n - 5] - ex[5:n - 5])) < 1e-8 * max(1, np.max(np.abs(ex)))
+    f = (x - 2.1) ** 7
+    D, _ = o.fd6_ko8_1d(f, h, 0.01, periodic=False)
+    assert np.max(np.abs(D[5:n - 5] - 7 * (x[5:n - 5] - 2.1) ** 6)) > 1e-6
+    errs = []
+    for n in (32, 64, 128):
+        h = 1.0 / n
+        x = np.arange(n) * h
+        D, _ = o.fd6_ko8_1d(np.sin(2 * np.pi * x), h, 0.01)
+        errs.append(np.max(np.abs(D - 2 * np.pi * np.cos(2 * np.pi * x))))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 5.8), orders
+
+
+def test_ko8_annihilates_degree_seven_and_has_its_fourier_symbol():
+    n, h, sigma = 48, 0.1, 0.37
+    x = np.arange(n) * h
+    for deg in range(8):
+        _, Q = o.fd6_ko8_1d((x - 2.1) ** deg, h, sigma, periodic=False)
+        assert np.max(np.abs(Q[5:n - 5])) < 1e-9
+    n = 64
+    h = 1.0 / n
+    x = np.arange(n) * h
+    for k in (1, 5, 16, 31):
+        f = np.cos(2 * np.pi * k * x + 0.3)
+        _, Q = o.fd6_ko8_1d(f, h, sigma)
+        symbol = sigma * (2.0 * np.sin(np.pi * k * h)) ** 8 / (256.0 * h)
+        assert np.max(np.abs(Q - symbol * f)) < 1e-12 * max(1.0, symbol)
