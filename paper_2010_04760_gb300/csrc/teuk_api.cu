@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "teuk_internal.h"
 
 namespace teuk {
@@ -26,6 +28,13 @@ static teuk_status cuda_fail(cudaError_t e, const char* what) {
         cudaError_t e_ = (call);                                \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
     } while (0)
+
+// NVTX range for the lifetime of a scope (host-side tracing of the public
+// calls; a no-op unless a profiler collects NVTX).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // State-sized scratch arrays one step of p's integrator needs.
 static int scratch_states(const teuk_params& p) { return p.rk == TEUK_RK_SSP104 ? 3 : 2; }
@@ -175,6 +184,7 @@ teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_d
 
 teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_dev,
                           double* u_dev, double* work_dev, int64_t nsteps, void* stream) {
+    NvtxRange trace("teuk_step_dev");
     teuk_status st = teuk_check_params(p);
     if (st != TEUK_OK) return st;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
@@ -292,6 +302,7 @@ teuk_status teuk_batch_destroy(teuk_batch* b) {
 
 teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int autotune,
                               teuk_batch** out) {
+    NvtxRange trace("teuk_batch_create");
     if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!ps || n < 1) return fail(TEUK_ERR_ARG, "need n >= 1 parameter sets");
@@ -409,6 +420,7 @@ teuk_status teuk_batch_get_state(teuk_batch* b, int k, double* u_host, double* t
 }
 
 teuk_status teuk_batch_step(teuk_batch* b, int64_t nsteps) {
+    NvtxRange trace("teuk_batch_step");
     if (!b) return fail(TEUK_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
     const int kChunk = 16;
@@ -460,6 +472,7 @@ teuk_status teuk_destroy(teuk_handle* h) {
 }
 
 teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
+    NvtxRange trace("teuk_create");
     if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
     *out = nullptr;
     teuk_status st = teuk_check_params(p);
@@ -541,6 +554,7 @@ teuk_status teuk_set_initial(teuk_handle* h, const double* psi, const double* pi
 }
 
 teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
+    NvtxRange trace("teuk_step");
     if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
     if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
     const int kChunk = 16;
@@ -572,6 +586,7 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
 
 teuk_status teuk_observe(teuk_handle* h, double rstar_ext, double* wave, double* horizon,
                          double* t_out) {
+    NvtxRange trace("teuk_observe");
     if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
     if (!std::isfinite(rstar_ext)) return fail(TEUK_ERR_ARG, "rstar_ext not finite");
     const int nr = h->p.nr, nth = h->p.ntheta;
