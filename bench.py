@@ -47,7 +47,7 @@ BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel source it
 # was taken on, identified by its sha256.
 NCU_TRAFFIC = {"source": "paper_2010_04760_gb300/csrc/teuk_stage.cu",
-               "sha256": "bb5efd8194392ef932f847e06585dd4815ac440aeaecfa0e9f80daf483edfdbe",
+               "sha256": "49b7b6ff128e8cc67261d2a8328cb1069cfc17bb03425fad826f34a90478dfe4",
                "bytes_per_launch": (31477504 + 39867392 + 39869696) / 3.0}
 
 

@@ -221,6 +221,18 @@ teuk_status teuk_get_info(const teuk_handle* h, teuk_params* p_out,
 teuk_status teuk_set_initial(teuk_handle* h, const double* psi,
                              const double* pi);
 
+/* Initial data of the paper's kind (Sec. 4: a Gaussian wave packet times
+ * spin-weighted harmonics), built on the host and copied in:
+ *   Psi(r*, theta) = sum_{k<nl} c_k exp(-(r* - rc)^2 / (2 width^2)) sY_{l_k m}(theta),
+ *   l_k = max(|s|, |m|) + k,  pi = 0,  t = 0,
+ * sY_lm by the Goldberg et al. (1967) sum formula at phi = 0. coeffs: 2*nl
+ * doubles (re, im) per term; if coeffs is NULL, c_k = A_k exp(i phi_k) with
+ * A_k = 0.5 + U, phi_k = 2 pi U', U, U' successive uniforms in [0, 1) from
+ * SplitMix64 seeded with `seed` (u = (x >> 11) * 2^-53 per 64-bit output x).
+ * nl in 1..16, width > 0. Synchronous. */
+teuk_status teuk_set_gaussian(teuk_handle* h, double rc, double width, const double* coeffs,
+                              int nl, uint64_t seed);
+
 /* Checkpoint: copy the planar state u[4][ntheta][nr] and time t in or out
  * (host memory, synchronous). Restoring a saved state and stepping gives
  * bitwise the same result as never having stopped. */

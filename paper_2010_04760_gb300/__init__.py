@@ -73,6 +73,7 @@ def lib():
             "teuk_get_info": (I, [P, PP, P, P]),
             "teuk_set_initial": (I, [P, P, P]),
             "teuk_set_state": (I, [P, P, D]),
+            "teuk_set_gaussian": (I, [P, D, D, P, I, ctypes.c_uint64]),
             "teuk_get_state": (I, [P, P, P]),
             "teuk_step": (I, [P, I64]),
             "teuk_observe": (I, [P, D, P, P, P]),
@@ -250,6 +251,19 @@ def teuk_set_initial(h, psi, pi):
     pc = np.ascontiguousarray(np.asarray(pi, dtype=np.complex128))
     _check(lib().teuk_set_initial(h.ptr, ps.ctypes.data_as(ctypes.c_void_p),
                                   pc.ctypes.data_as(ctypes.c_void_p)))
+
+
+def teuk_set_gaussian(h, rc, width, coeffs=None, nl=None, seed=0):
+    """coeffs: complex amplitudes per l (from max(|s|, |m|) upward), or None to
+    draw them from SplitMix64(seed) (then nl terms)."""
+    if coeffs is not None:
+        c = np.asarray(coeffs, dtype=np.complex128)
+        arr = np.ascontiguousarray(np.stack([c.real, c.imag], axis=-1).ravel())
+        n = c.size
+        ptr = arr.ctypes.data_as(ctypes.c_void_p)
+    else:
+        n, ptr = int(nl or 1), None
+    _check(lib().teuk_set_gaussian(h.ptr, float(rc), float(width), ptr, n, int(seed)))
 
 
 def teuk_set_state(h, u, t=0.0):

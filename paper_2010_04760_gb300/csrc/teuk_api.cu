@@ -553,6 +553,53 @@ teuk_status teuk_set_initial(teuk_handle* h, const double* psi, const double* pi
     return teuk_set_state(h, u.data(), 0.0);
 }
 
+teuk_status teuk_set_gaussian(teuk_handle* h, double rc, double width, const double* coeffs,
+                              int nl, uint64_t seed) {
+    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+    if (nl < 1 || nl > 16) return fail(TEUK_ERR_ARG, "nl must be in 1..16");
+    if (!(width > 0.0) || !std::isfinite(width) || !std::isfinite(rc))
+        return fail(TEUK_ERR_ARG, "need finite rc and width > 0");
+    const teuk_params& p = h->p;
+    const int nr = p.nr, nth = p.ntheta;
+    const size_t n = h->plane();
+    std::vector<double> cre(nl), cim(nl);
+    uint64_t state = seed;
+    for (int k = 0; k < nl; ++k) {
+        if (coeffs) {
+            cre[k] = coeffs[2 * k];
+            cim[k] = coeffs[2 * k + 1];
+        } else {
+            const double amp = 0.5 + (double)(splitmix64(state) >> 11) * 0x1.0p-53;
+            const double ph = 2.0 * M_PI * (double)(splitmix64(state) >> 11) * 0x1.0p-53;
+            cre[k] = amp * std::cos(ph);
+            cim[k] = amp * std::sin(ph);
+        }
+    }
+    const int l0 = std::max(std::abs(p.s), std::abs(p.m));
+    const double hs = (p.rstar_max - p.rstar_min) / (nr - 1);
+    std::vector<double> radial(nr), ang((size_t)nl * nth);
+    for (int i = 0; i < nr; ++i) {
+        const double z = (p.rstar_min + i * hs - rc) / width;
+        radial[i] = std::exp(-0.5 * z * z);
+    }
+    for (int k = 0; k < nl; ++k)
+        for (int j = 0; j < nth; ++j)
+            ang[(size_t)k * nth + j] = swsh(p.s, l0 + k, p.m, (j + 0.5) * M_PI / nth);
+    std::vector<double> u(4 * n, 0.0);
+    for (int j = 0; j < nth; ++j) {
+        double are = 0.0, aim = 0.0;
+        for (int k = 0; k < nl; ++k) {
+            are += cre[k] * ang[(size_t)k * nth + j];
+            aim += cim[k] * ang[(size_t)k * nth + j];
+        }
+        for (int i = 0; i < nr; ++i) {
+            u[(size_t)j * nr + i] = are * radial[i];
+            u[n + (size_t)j * nr + i] = aim * radial[i];
+        }
+    }
+    return teuk_set_state(h, u.data(), 0.0);
+}
+
 teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
     NvtxRange trace("teuk_step");
     if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");

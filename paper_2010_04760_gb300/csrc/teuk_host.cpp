@@ -117,6 +117,35 @@ PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_par
     return c;
 }
 
+// Spin-weighted spherical harmonic sY_lm(theta, phi = 0), Goldberg et al.
+// (1967): (-1)^m sqrt[(l+m)!(l-m)!(2l+1) / (4 pi (l+s)!(l-s)!)]
+//   x sum_r C(l-s, r) C(l+s, r+s-m) (-1)^(l-r-s) sin^(2l-k)(th/2) cos^k(th/2),
+// k = 2r + s - m (sin^2l(x) cot^k(x) written without negative powers).
+double swsh(int s, int l, int m, double theta) {
+    auto fact = [](int n) { double f = 1.0; for (int k = 2; k <= n; ++k) f *= k; return f; };
+    auto binom = [&](int n, int k) { return (k < 0 || k > n) ? 0.0 : fact(n) / (fact(k) * fact(n - k)); };
+    const double x = 0.5 * theta, sx = std::sin(x), cx = std::cos(x);
+    const double norm = std::sqrt(fact(l + m) * fact(l - m) * (2 * l + 1) /
+                                  (4.0 * M_PI * fact(l + s) * fact(l - s)));
+    double sum = 0.0;
+    for (int r = 0; r <= l - s; ++r) {
+        const int k2 = r + s - m;
+        if (k2 < 0 || k2 > l + s) continue;
+        const int k = 2 * r + s - m;
+        const double sign = ((l - r - s) % 2 == 0) ? 1.0 : -1.0;
+        sum += binom(l - s, r) * binom(l + s, k2) * sign * std::pow(sx, 2 * l - k) * std::pow(cx, k);
+    }
+    return ((m % 2 == 0) ? 1.0 : -1.0) * norm * sum;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): one 64-bit output per call.
+uint64_t splitmix64(uint64_t& state) {
+    uint64_t z = (state += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
 // r and r - r_+ at every r* node.
 static void radial_nodes(const teuk_params& p, std::vector<double>& r, std::vector<double>& x) {
     const double h = (p.rstar_max - p.rstar_min) / (p.nr - 1);

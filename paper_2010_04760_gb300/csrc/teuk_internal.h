@@ -1,6 +1,7 @@
 // Internal declarations shared by the host (.cpp) and device (.cu) parts of
 // the library. Not part of the public ABI.
 #pragma once
+#include <cstdint>
 #include <string>
 #include "../../include/teuk.h"
 
@@ -39,6 +40,9 @@ struct PointCoef {
 double r_of_rstar(double rstar, double M, double a, double* x_out);
 PointCoef point_coefficients(double rstar, double theta, const teuk_params& p);
 PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_params& p);
+
+double swsh(int s, int l, int m, double theta);
+uint64_t splitmix64(uint64_t& state);
 
 // Batched evolutions: pointers and step of one member.
 struct BatchEvo {

@@ -98,6 +98,36 @@ def initial_data(w: Workload):
     return u
 
 
+def splitmix64_uniforms(seed, count):
+    """Uniforms in [0, 1) from SplitMix64 (Steele, Lea, Flood 2014):
+    u = (x >> 11) 2^-53 for each 64-bit output x."""
+    mask = (1 << 64) - 1
+    state = seed & mask
+    out = []
+    for _ in range(count):
+        state = (state + 0x9E3779B97F4A7C15) & mask
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z = z ^ (z >> 31)
+        out.append((z >> 11) * 2.0 ** -53)
+    return out
+
+
+def gaussian_data(w: Workload, rc, width, coeffs):
+    """u[4, nth, nr]: Psi = sum_k coeffs[k] exp(-(r* - rc)^2 / (2 width^2))
+    sY_{l0+k, m}(theta) with l0 = max(|s|, |m|), pi = 0."""
+    rs = rstar_nodes(w.nr, w.rs_min, w.rs_max)
+    th = theta_nodes(w.nth)
+    radial = np.exp(-0.5 * ((rs - rc) / width) ** 2)
+    l0 = max(abs(w.s), abs(w.m))
+    ang = sum(c * swsh(w.s, l0 + k, w.m, th) for k, c in enumerate(coeffs))
+    psi = np.outer(ang, radial)
+    u = np.zeros((4, w.nth, w.nr))
+    u[0], u[1] = psi.real, psi.imag
+    return u
+
+
 def random_state(nr, nth, seed, smooth=True):
     """A generic seeded state for operator-level parity checks: a sum of a
     few Gaussians and sinusoids in r* times smooth theta profiles, plus (if

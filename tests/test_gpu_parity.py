@@ -325,3 +325,23 @@ def test_device_entry_points_reject_bad_arguments():
         assert ei.value.status == T.TEUK_ERR_ARG
     with pytest.raises(T.TeukError):
         T.teuk_stage_dev(p, 0.1, coef, None, u, u, 1)       # out aliases u_prev
+
+
+@pytest.mark.parametrize("a,s,m", [(0.999, -2, 2), (0.0, 0, 0), (0.5, -1, 3)])
+def test_set_gaussian_matches_python_construction(a, s, m):
+    wl = I.KERR_GRAV.with_(nr=257, nth=33, a=a, s=s, m=m)
+    p = T.params_from_workload(wl)
+    h = T.teuk_create(p)
+    coeffs = [0.7 - 0.2j, 1.1 + 0.4j, -0.3 + 0.9j]
+    T.teuk_set_gaussian(h, 30.0, 3.0, coeffs)
+    got, t = T.teuk_get_state(h)
+    exp_ = I.gaussian_data(wl, 30.0, 3.0, coeffs)
+    assert t == 0.0
+    assert np.max(np.abs(got - exp_)) <= 1e-13 * np.max(np.abs(exp_))
+    # seeded: amplitudes 0.5 + U, phases 2 pi U' from SplitMix64
+    T.teuk_set_gaussian(h, -10.0, 4.0, None, nl=2, seed=2026)
+    us = I.splitmix64_uniforms(2026, 4)
+    seeded = [(0.5 + us[2 * k]) * np.exp(2j * np.pi * us[2 * k + 1]) for k in range(2)]
+    got, _ = T.teuk_get_state(h)
+    exp_ = I.gaussian_data(wl, -10.0, 4.0, seeded)
+    assert np.max(np.abs(got - exp_)) <= 1e-13 * np.max(np.abs(exp_))
