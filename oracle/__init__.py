@@ -7,7 +7,9 @@ package. It shares no code with the CUDA library under
 passage each routine follows.
 
 Layout: state ``u[4, nth, nr]`` (Psi_R, Psi_I, pi_R, pi_I); coefficients
-``coef[9, nth, nr]`` = b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth.
+``coef[10, nth, nr]`` = b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth, c
+(c: the pi rows' speed, equal to b in r*). Radial coordinate: r* (coords 0) or
+the hyperboloidal rho (coords 1), its range in ``rs_min, rs_max`` either way.
 Weight precision codes: 0 binary64, 1 binary32, 2 binary16, 3 bfloat16.
 """
 import ctypes
@@ -41,7 +43,8 @@ class Grid(ctypes.Structure):
                 ("s", ctypes.c_int), ("m", ctypes.c_int),
                 ("eps", ctypes.c_double), ("wprec", ctypes.c_int),
                 ("theta_mode", ctypes.c_int), ("scheme", ctypes.c_int),
-                ("ko_sigma", ctypes.c_double)]
+                ("ko_sigma", ctypes.c_double), ("coords", ctypes.c_int),
+                ("field", ctypes.c_int), ("S", ctypes.c_double)]
 
 
 def _load():
@@ -53,7 +56,9 @@ def _load():
         sig = {
             "orc_rstar_of_r": (D, [D, D, D]),
             "orc_r_of_rstar": (D, [D, D, D]),
-            "orc_coeff_point": (None, [D, D, D, D, I, I, P]),
+            "orc_coeff_point": (None, [D, D, D, D, I, I, I, P]),
+            "orc_coeff_point_hyp": (None, [D, D, D, D, D, I, I, P]),
+            "orc_rho_of_r": (D, [D, D]),
             "orc_coefficients": (None, [P, P]),
             "orc_round_w": (D, [I, D]),
             "orc_weno5_weights": (None, [I, I, P, D, P]),
@@ -86,10 +91,22 @@ def _f64(a):
 
 
 def grid(nr, nth, rs_min, rs_max, M=1.0, a=0.0, s=0, m=0, eps=1e-6, wprec="fp64", theta_mode=0,
-         scheme=0, ko_sigma=0.01):
+         scheme=0, ko_sigma=0.01, coords=0, field=0, S=20.0):
+    """Grid description. coords 1 (hyperboloidal) always evolves Phi."""
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    if int(coords) == 1:
+        field = 1
     return Grid(nr, nth, rs_min, rs_max, M, a, s, m, eps, w, int(theta_mode), int(scheme),
-                float(ko_sigma))
+                float(ko_sigma), int(coords), int(field), float(S))
+
+
+def rho_of_r(r, S):
+    return _load().orc_rho_of_r(float(r), float(S))
+
+
+def horizon_rho(M, a, S):
+    """rho of the outer horizon r_+ = M + sqrt(M^2 - a^2)."""
+    return rho_of_r(M + np.sqrt(max(M * M - a * a, 0.0)), S)
 
 
 def num_threads():
@@ -104,14 +121,20 @@ def r_of_rstar(rs, M=1.0, a=0.0):
     return _load().orc_r_of_rstar(rs, M, a)
 
 
-def coeff_point(r, th, M, a, s, m):
-    out = np.zeros(9)
-    _load().orc_coeff_point(r, th, M, a, s, m, _ptr(out))
+def coeff_point(r, th, M, a, s, m, field=0):
+    out = np.zeros(10)
+    _load().orc_coeff_point(r, th, M, a, s, m, int(field), _ptr(out))
+    return out
+
+
+def coeff_point_hyp(rho, th, M, a, S, s, m):
+    out = np.zeros(10)
+    _load().orc_coeff_point_hyp(rho, th, M, a, S, s, m, _ptr(out))
     return out
 
 
 def coefficients(g):
-    coef = np.zeros((9, g.nth, g.nr))
+    coef = np.zeros((10, g.nth, g.nr))
     _load().orc_coefficients(ctypes.byref(g), _ptr(coef))
     return coef
 
@@ -137,7 +160,9 @@ def fd6_ko8_1d(f, h, sigma=0.01, periodic=True):
 
 
 def weno5_deriv_1d(f, h, dir, wprec="fp64", eps=1e-6, periodic=True, force_w=None,
-                   return_wq=False):
+                   return_wq=False, bc=None):
+    """bc: 0 edge copy, 1 periodic, 2 polynomial extrapolation (default from
+    ``periodic``)."""
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
     f = _f64(f)
     n = f.size
@@ -145,7 +170,8 @@ def weno5_deriv_1d(f, h, dir, wprec="fp64", eps=1e-6, periodic=True, force_w=Non
     fw = None if force_w is None else _f64(force_w)
     wo = np.zeros((n, 3)) if return_wq else None
     qo = np.zeros((n, 3)) if return_wq else None
-    _load().orc_weno5_deriv_1d(_ptr(f), n, h, dir, w, eps, int(periodic),
+    bc = int(periodic) if bc is None else int(bc)
+    _load().orc_weno5_deriv_1d(_ptr(f), n, h, dir, w, eps, bc,
                                None if fw is None else _ptr(fw), _ptr(D),
                                None if wo is None else _ptr(wo),
                                None if qo is None else _ptr(qo))

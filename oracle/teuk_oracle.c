@@ -7,13 +7,22 @@
  * plain loops; the passage each one follows is cited beside it.
  *
  * Readings of points the paper leaves open (each is listed in the design doc):
- *  - Coordinates: Boyer-Lindquist time t, tortoise r*, ingoing azimuth
- *    phi~ (Sec. 2.2), in place of the hyperboloidal (tau, rho) whose
- *    coefficients the paper does not print.
- *  - First-order variable pi = Psi_t + b Psi_* with b = +sqrt(A**) > 0, so the
- *    Psi rows have speed +b and the pi rows -b, as Sec. 3.1 states.
- *  - r* boundaries: ghost values copy the edge value (zeroth-order
- *    extrapolation). theta: cell-centred grid, ghost rows mirror across the
+ *  - Coordinates (coords 0): Boyer-Lindquist time t, tortoise r*, ingoing
+ *    azimuth phi~ (Sec. 2.2). coords 1: the paper's hyperboloidal slices
+ *    (tau, rho) of Sec. 2.2, whose coefficients (Eq. near_final) the paper
+ *    does not print; they are derived here from Eq. teuk0 for the field
+ *    Phi = r Delta^s Psi (the paper's Phi of Sec. 4 at s = -2), and the grid
+ *    runs from the horizon rho_+ to at most scri (rho = S). The "4 ln" of the
+ *    slice's height function is read as 4 M ln (the paper sets M = 1).
+ *  - Field (field 1): Phi = r Delta^s Psi in either coordinate system.
+ *  - First-order variable pi = Psi_t + b Psi_* with b the larger root of
+ *    b^2 + Atr b - Arr = 0 (b = +sqrt(A**) > 0 in r*), so the Psi rows move
+ *    with speed +b (outgoing) and the pi rows with -c, c = Atr + b (ingoing);
+ *    in r* c = b, as Sec. 3.1 states.
+ *  - Radial boundaries: in r*, ghost values copy the edge value (zeroth-order
+ *    extrapolation). On the hyperboloidal grid both ends are outflow
+ *    boundaries (horizon and scri); ghosts extrapolate the polynomial through
+ *    the edge nodes. theta: cell-centred grid, ghost rows mirror across the
  *    poles with parity (-1)^(m+s).
  *  - theta derivatives: fourth-order centred differences (the paper says
  *    "standard centered differencing" without an order). Optional theta WENO
@@ -96,10 +105,15 @@ double orc_r_of_rstar(double rs, double M, double a) {
 /*   psi_t = pi - b psi_*,                                                   */
 /*   pi_t  = b pi_* + K psi_* + Ath psi_thth + Bth psi_th + Bt pi + C psi,   */
 /*   K = B* - b b_* - b Bt,  b_* = d b / d r* = (Delta/varpi) d b / d r.     */
-/* out = {b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth}.                */
+/* field 1 evolves Phi = Psi / g, g = Delta^-s / r: with                      */
+/*   g1 = (dg/dr*) / g = -(s Delta' + Delta/r)/varpi,                        */
+/*   g2 = (d2g/dr*2) / g = dg1/dr* + g1^2,                                   */
+/* the Phi equation has B* + 2 A** g1 in place of B* and C + A** g2 + B* g1  */
+/* in place of C (Bt, Ath, Bth unchanged: there is no t-r* cross term).      */
+/* out = {b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth, c}, c = b.      */
 /* ------------------------------------------------------------------------ */
 void orc_coeff_point(double r, double th, double M, double a, int s, int m,
-                     double out[9]) {
+                     int field, double out[10]) {
     double sn = sin(th), cs = cos(th);
     double varpi = r * r + a * a;
     double Delta = r * r - 2.0 * M * r + a * a;
@@ -116,6 +130,18 @@ void orc_coeff_point(double r, double th, double M, double a, int s, int m,
     double mc = m + s * cs;
     double complex C = (4.0 * I * s * m * a * (r - M)
                         + Delta * (s - mc * mc / (sn * sn))) / Sigma2;
+    double Axx = varpi * varpi / Sigma2;
+
+    if (field == 1) {
+        /* g1(r) = -N/varpi, N = 2s(r-M) + Delta/r = 2s(r-M) + r - 2M + a^2/r */
+        double N = 2.0 * s * (r - M) + r - 2.0 * M + a * a / r;
+        double dN = 2.0 * s + 1.0 - a * a / (r * r);
+        double g1 = -N / varpi;
+        double dg1_dr = -(dN * varpi - N * 2.0 * r) / (varpi * varpi);
+        double g2 = (Delta / varpi) * dg1_dr + g1 * g1;
+        C = C + Axx * g2 + Bstar * g1;
+        Bstar = Bstar + 2.0 * Axx * g1;
+    }
 
     double b = varpi / Sigma;
     double dSigma2_dr = 2.0 * varpi * (2.0 * r) - a * a * sn * sn * 2.0 * (r - M);
@@ -128,21 +154,118 @@ void orc_coeff_point(double r, double th, double M, double a, int s, int m,
     out[3] = creal(Bt); out[4] = cimag(Bt);
     out[5] = creal(C);  out[6] = cimag(C);
     out[7] = Ath;       out[8] = Bth;
+    out[9] = b;
 }
 
-/* Grid (reading): r*_i = rs_min + i h, h = (rs_max - rs_min)/(nr-1);       */
-/* theta_j = (j + 1/2) pi / nth (cell centred, never on a pole).            */
+/* ------------------------------------------------------------------------ */
+/* Hyperboloidal slices (Sec. 2.2): ingoing Kerr t~ = t - r + r*,            */
+/* phi~ = phi + int a/Delta dr, then                                         */
+/*   tau = t~ - r^2/(r+S) + 4M ln(S/(r+S)),   rho = r/(1 + r/S),             */
+/* and the field Phi = r Delta^s Psi (Sec. 4). Written as                    */
+/*   A^tt Phi_tt + A^tr Phi_tr + A^rr Phi_rr + Phi_thth + cot Phi_th         */
+/*   + B^t Phi_t + B^r Phi_r + C Phi = 0   (t = tau, r = rho here)           */
+/* this is Eq. near_final; dividing by D = -A^tt > 0 gives Eq. final.        */
+/* Derived by the chain rule from Eq. teuk0 with tau = t + T(r),             */
+/* T' = varpi/Delta - H', H' = 2 - W^2 + 4MW/S, rho' = W^2, W = S/(r+S)      */
+/* = 1 - rho/S, and written in x = 1/r = 1/rho - 1/S, W and rho so that      */
+/* every term stays finite and free of cancellation from the horizon to      */
+/* scri (x = 0, W = 0, rho = S):                                             */
+/*   delta = Delta/r^2 = 1 - 2Mx + a^2 x^2,  w = varpi/r^2 = 1 + a^2 x^2,    */
+/*   sig = Sigma/r^2 = sqrt(w^2 - a^2 x^2 delta sin^2),                      */
+/*   G  = 2 varpi - Delta H'                                                 */
+/*      = rho (rho + 4M + 8M^2/S - 2MW + a^2 x (W - 4M/S)),                  */
+/*   E  = Sigma + varpi - Delta H' = G - a^2 delta sin^2 / (sig + w),        */
+/*   D  = H' G - a^2 sin^2,                                                  */
+/*   A^tr = 2 W^2 (varpi - Delta H'),  A^rr = rho^2 W^2 delta,               */
+/*   B^t = 2s rho (4M/S - W) - 2(1+s) M H' + 2a^2 x (H' - 1)                 */
+/*         - 2 delta rho^2 (W - 2M/S)/S + i (2ma (1 - H') - 2sa cos),        */
+/*   B^r = 2ima W^2 - 2W rho ((s+1) - W - rho x (2M - a^2 x)/S)              */
+/*         + 2W^2 (M (1+s) - a^2 x),                                         */
+/*   C   = s - (m + s cos)^2/sin^2 - 2(s+1) M x + 2a^2 x^2 - 2imax.          */
+/* The principal symbol's discriminant is A^tr^2 - 4 A^rr A^tt               */
+/* = 4 W^4 Sigma^2, so the roots of b^2 + (A^tr/D) b - A^rr/D = 0 are        */
+/*   b = W^2 Delta / E = rho^2 delta / E  (outgoing, 0 on the horizon),      */
+/*   -c, c = W^2 E / D                    (ingoing, 0 at scri).              */
+/* First-order form with pi = Phi_tau + b Phi_rho:                           */
+/*   Phi_tau = pi - b Phi_rho,                                               */
+/*   pi_tau  = c pi_rho + K Phi_rho + Phi_thth/D + cot Phi_th/D              */
+/*             + (B^t/D) pi + (C/D) Phi,  K = B^r/D - b B^t/D - c b_rho.     */
+/* b_rho by the complex-step derivative (Squire and Trapp 1998):             */
+/* b_rho = Im b(rho + i h)/h, exact to rounding for analytic b.              */
+/* out = {b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth, c} with         */
+/* Bt = B^t/D, C = C/D, Ath = 1/D, Bth = cot/D.                              */
+/* ------------------------------------------------------------------------ */
+double orc_rho_of_r(double r, double S) { return r / (1.0 + r / S); }
+
+static double complex hyp_b(double complex rho, double sn2, double M, double a,
+                            double S) {
+    double complex x = 1.0 / rho - 1.0 / S;
+    double complex W = 1.0 - rho / S;
+    double complex delta = 1.0 - 2.0 * M * x + a * a * x * x;
+    double complex w = 1.0 + a * a * x * x;
+    double complex sig = csqrt(w * w - a * a * x * x * delta * sn2);
+    double complex G = rho * (rho + 4.0 * M + 8.0 * M * M / S - 2.0 * M * W
+                              + a * a * x * (W - 4.0 * M / S));
+    double complex E = G - a * a * delta * sn2 / (sig + w);
+    return rho * rho * delta / E;
+}
+
+void orc_coeff_point_hyp(double rho, double th, double M, double a, double S,
+                         int s, int m, double out[10]) {
+    double sn = sin(th), cs = cos(th), sn2 = sn * sn;
+    double x = 1.0 / rho - 1.0 / S;
+    double W = 1.0 - rho / S;
+    double delta = 1.0 - 2.0 * M * x + a * a * x * x;
+    double w = 1.0 + a * a * x * x;
+    double sig = sqrt(w * w - a * a * x * x * delta * sn2);
+    double Hp = 2.0 - W * W + 4.0 * M * W / S;
+    double G = rho * (rho + 4.0 * M + 8.0 * M * M / S - 2.0 * M * W
+                      + a * a * x * (W - 4.0 * M / S));
+    double E = G - a * a * delta * sn2 / (sig + w);
+    double D = Hp * G - a * a * sn2;
+
+    double b = rho * rho * delta / E;
+    double c = W * W * E / D;
+    double hstep = 1e-30;
+    double db = cimag(hyp_b(rho + I * hstep, sn2, M, a, S)) / hstep;
+
+    double complex Bt = (2.0 * s * rho * (4.0 * M / S - W) - 2.0 * (1 + s) * M * Hp
+                         + 2.0 * a * a * x * (Hp - 1.0)
+                         - 2.0 * delta * rho * rho * (W - 2.0 * M / S) / S
+                         + I * (2.0 * m * a * (1.0 - Hp) - 2.0 * s * a * cs)) / D;
+    double complex Br = (2.0 * I * m * a * W * W
+                         - 2.0 * W * rho * ((s + 1) - W - rho * x * (2.0 * M - a * a * x) / S)
+                         + 2.0 * W * W * (M * (1 + s) - a * a * x)) / D;
+    double mc = m + s * cs;
+    double complex C = (s - mc * mc / sn2 - 2.0 * (s + 1) * M * x + 2.0 * a * a * x * x
+                        - 2.0 * I * m * a * x) / D;
+    double complex K = Br - b * Bt - c * db;
+
+    out[0] = b;
+    out[1] = creal(K);  out[2] = cimag(K);
+    out[3] = creal(Bt); out[4] = cimag(Bt);
+    out[5] = creal(C);  out[6] = cimag(C);
+    out[7] = 1.0 / D;   out[8] = (cs / sn) / D;
+    out[9] = c;
+}
+
+/* Grid (reading): x_i = x_min + i h, h = (x_max - x_min)/(nr-1), x = r* or  */
+/* rho; theta_j = (j + 1/2) pi / nth (cell centred, never on a pole).       */
 void orc_coefficients(const orc_grid* g, double* coef) {
     int nr = g->nr, nth = g->nth;
     double h = (g->rs_max - g->rs_min) / (nr - 1);
     long plane = (long)nr * nth;
     for (int i = 0; i < nr; ++i) {
-        double r = orc_r_of_rstar(g->rs_min + i * h, g->M, g->a);
+        double x = g->rs_min + i * h;
+        double r = (g->coords == 1) ? 0.0 : orc_r_of_rstar(x, g->M, g->a);
         for (int j = 0; j < nth; ++j) {
             double th = (j + 0.5) * M_PI / nth;
-            double c[9];
-            orc_coeff_point(r, th, g->M, g->a, g->s, g->m, c);
-            for (int k = 0; k < 9; ++k) coef[k * plane + (long)j * nr + i] = c[k];
+            double c[10];
+            if (g->coords == 1)
+                orc_coeff_point_hyp(x, th, g->M, g->a, g->S, g->s, g->m, c);
+            else
+                orc_coeff_point(r, th, g->M, g->a, g->s, g->m, g->field, c);
+            for (int k = 0; k < 10; ++k) coef[k * plane + (long)j * nr + i] = c[k];
         }
     }
 }
@@ -300,20 +423,40 @@ double orc_weno5_flux(int wprec, int dir, const double* f, double eps,
     return w[0] * q[0] + w[1] * q[1] + w[2] * q[2];
 }
 
+/* Ghost value at index k outside 0..n-1 by Lagrange extrapolation of the  */
+/* degree-q polynomial through the q+1 nearest edge nodes:                   */
+/*   p(k) = sum_j f_j prod_{l != j} (k - x_l)/(x_j - x_l).                   */
+/* The hyperboloidal grid uses q = 4 (reading: both of its ends are outflow  */
+/* boundaries, which need no data; among degrees 0..4 the quartic gave the   */
+/* fastest convergence of the horizon value under grid refinement).          */
+#define EXTRAP_DEG 4
+static double extrap_ghost(const double* f, int n, int k, int q) {
+    int x0 = (k < 0) ? 0 : n - 1 - q;          /* nodes x0 .. x0+q */
+    double v = 0.0;
+    for (int j = x0; j <= x0 + q; ++j) {
+        double L = 1.0;
+        for (int l = x0; l <= x0 + q; ++l)
+            if (l != j) L *= (double)(k - l) / (double)(j - l);
+        v += L * f[j];
+    }
+    return v;
+}
+
 /* Derivative of one line, D_i = (fhat_{i+1/2} - fhat_{i-1/2}) / h           */
-/* (Sec. 3.1.2). Ghosts: periodic wrap, or copies of the edge value.         */
+/* (Sec. 3.1.2). Ghosts (bc): 0 copies of the edge value, 1 periodic wrap,   */
+/* 2 polynomial extrapolation (extrap_ghost).                                */
 /* w_out / q_out (optional, 3 per interface) receive the weights and          */
 /* candidate values of interface i+1/2 for i = 0..n-1.                       */
 void orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
-                        double eps, int periodic, const double* force_w,
+                        double eps, int bc, const double* force_w,
                         double* D, double* w_out, double* q_out) {
     double* ext = (double*)malloc(sizeof(double) * (n + 6));
     double* fh = (double*)malloc(sizeof(double) * (n + 1));
     for (int k = -3; k < n + 3; ++k) {
-        int src = k;
-        if (periodic) src = ((k % n) + n) % n;
-        else src = k < 0 ? 0 : (k >= n ? n - 1 : k);
-        ext[k + 3] = f[src];
+        if (k >= 0 && k < n) ext[k + 3] = f[k];
+        else if (bc == 1) ext[k + 3] = f[((k % n) + n) % n];
+        else if (bc == 2) ext[k + 3] = extrap_ghost(f, n, k, EXTRAP_DEG);
+        else ext[k + 3] = f[k < 0 ? 0 : n - 1];
     }
     /* interface i+1/2 for i = -1 .. n-1, stored at fh[i+1] */
     for (int i = -1; i < n; ++i) {
@@ -370,7 +513,8 @@ void orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int periodic
 /* (Sec. 3.1.2); m31, m32 use the same Psi derivative. theta derivatives are */
 /* fourth-order centred with parity ghosts. Complex form:                    */
 /*   F_Psi = pi - b D_Psi,                                                   */
-/*   F_pi  = b D_pi + K D_Psi + Ath Psi_thth + Bth Psi_th + Bt pi + C Psi.   */
+/*   F_pi  = c D_pi + K D_Psi + Ath Psi_thth + Bth Psi_th + Bt pi + C Psi    */
+/* (c = b in r*).                                                            */
 /* ------------------------------------------------------------------------ */
 void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) {
     int nr = g->nr, nth = g->nth;
@@ -390,7 +534,8 @@ void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) 
             } else {
                 int dir = (c < 2) ? +1 : -1;
                 orc_weno5_deriv_1d(&u[c * plane + (long)j * nr], nr, h, dir, g->wprec,
-                                   g->eps, 0, NULL, &Dc[c * nr], NULL, NULL);
+                                   g->eps, g->coords == 1 ? 2 : 0, NULL, &Dc[c * nr],
+                                   NULL, NULL);
             }
         }
         /* rows j-2 .. j+2 of Psi, with ghosts across the poles */
@@ -449,9 +594,10 @@ void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) 
             double complex Bt = coef[3 * plane + p] + I * coef[4 * plane + p];
             double complex C = coef[5 * plane + p] + I * coef[6 * plane + p];
             double Ath = coef[7 * plane + p], Bth = coef[8 * plane + p];
+            double cpi = coef[9 * plane + p];
 
             double complex Fpsi = pi - b * Dpsi;
-            double complex Fpi = b * Dpi + K * Dpsi + Ath * psi_thth
+            double complex Fpi = cpi * Dpi + K * Dpsi + Ath * psi_thth
                                  + Bth * psi_th + Bt * pi + C * psi;
             /* scheme 1: the Kreiss-Oliger term is subtracted (dissipative sign) */
             F[0 * plane + p] = creal(Fpsi) - Qc[0 * nr + i];

@@ -11,7 +11,10 @@
  *   u[c][j][i], c in {Psi_R, Psi_I, pi_R, pi_I}, j = theta row (0..nth-1),
  *   i = r* index (0..nr-1, fastest).
  * Coefficient layout (complex first-order form, see orc_coeff_point):
- *   coef[k][j][i], k = 0..8 : b, K_re, K_im, Bt_re, Bt_im, C_re, C_im, Ath, Bth.
+ *   coef[k][j][i], k = 0..9 : b, K_re, K_im, Bt_re, Bt_im, C_re, C_im, Ath, Bth,
+ *   c (the pi rows' speed; c = b in r*).
+ * The radial coordinate is r* (coords 0) or the hyperboloidal rho (coords 1);
+ * rs_min, rs_max hold its range either way.
  *
  * Weight precision codes: 0 = binary64 (paper formulas), 1 = binary32,
  * 2 = binary16, 3 = bfloat16 (reduced-precision reading, see teuk_oracle.c),
@@ -35,12 +38,18 @@ typedef struct {
     int theta_mode;          /* 0: centred dtheta; 1: WENO5 dtheta (reading)     */
     int scheme;              /* 0: WENO5 in r*; 1: FD6 + KO8 (Sec. 3.1.1)        */
     double ko_sigma;         /* Kreiss-Oliger sigma of scheme 1                  */
+    int coords;              /* 0: BL t and r*; 1: hyperboloidal (tau, rho)      */
+    int field;               /* 0: Psi; 1: Phi = r Delta^s Psi (always in 1)     */
+    double S;                /* hyperboloidal slice parameter (coords 1)         */
 } orc_grid;
 
 double orc_rstar_of_r(double r, double M, double a);
 double orc_r_of_rstar(double rs, double M, double a);
 void   orc_coeff_point(double r, double th, double M, double a, int s, int m,
-                       double out[9]);
+                       int field, double out[10]);
+double orc_rho_of_r(double r, double S);
+void   orc_coeff_point_hyp(double rho, double th, double M, double a, double S,
+                           int s, int m, double out[10]);
 void   orc_coefficients(const orc_grid* g, double* coef);
 double orc_round_w(int wprec, double x);
 void   orc_weno5_weights(int wprec, int dir, const double* f5, double eps,
@@ -50,7 +59,7 @@ double orc_weno5_flux(int wprec, int dir, const double* f5, double eps,
 void   orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int periodic,
                       double* D, double* Q);
 void   orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
-                          double eps, int periodic, const double* force_w,
+                          double eps, int bc, const double* force_w,
                           double* D, double* w_out, double* q_out);
 void   orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F);
 void   orc_rk3_step(const orc_grid* g, const double* coef, double dt, double* u,

@@ -34,7 +34,7 @@ def host(t):
 
 def oracle_dt(g, co):
     """Test-side time step: 0.5 / max(b/h + sqrt(theta frequencies))."""
-    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth = co
+    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth = co[:9]
     h = (g.rs_max - g.rs_min) / (g.nr - 1)
     dth = np.pi / g.nth
     kap = Ath * (16 / 3) / dth ** 2 + np.abs(Bth) * 1.5 / dth + np.hypot(Cr, Ci)

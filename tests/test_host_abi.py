@@ -62,7 +62,7 @@ def test_coefficients_agree_with_oracle(a, s, m):
     p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m)
     got = T.teuk_build_coefficients(p, dt)
     co = o.coefficients(o.grid(nr, nth, rs0, rs1, 1.0, a, s, m))
-    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth = co
+    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth = co[:9]
     h = (rs1 - rs0) / (nr - 1)
     dth = np.pi / nth
     tol = dict(rtol=1e-9, atol=1e-14)

@@ -1,0 +1,256 @@
+"""Pins of the oracle's hyperboloidal (tau, rho) coefficients and rescaled field
+(Sec. 2.2 slices, Sec. 4's Phi = (r/Delta^2) Psi, generalised to r Delta^s Psi).
+
+The check plugs Psi = g(r) exp(k1 tau + k2 rho + k3 theta + i m phi~) into the
+Teukolsky master equation (Eq. teuk0) in Boyer-Lindquist coordinates, with
+tau, rho and phi~ written as functions of (t, r, phi) exactly as Sec. 2.2
+defines them, and lets sympy differentiate. Divided by Psi, the result is a
+polynomial of degree two in (k1, k2, k3) whose coefficients are those of
+Eq. near_final; they are read off by evaluating at a few k (exact for a
+quadratic) with 40-digit mpmath arithmetic. The first-order quantities of
+Sec. 2.3 then follow by their definitions (b the root of the characteristic
+quadratic, pi = Phi_tau + b Phi_rho), with d b / d rho by mpmath's numerical
+derivative. Nothing is taken from the oracle's closed forms.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+
+sp = pytest.importorskip("sympy")
+mp = pytest.importorskip("mpmath")
+
+
+def _operator(rescale):
+    """L[Psi]/Psi as an mpmath function of (k1, k2, k3, r, theta, M, a, S, s, m)."""
+    t, r, th, ph = sp.symbols("t r theta phi", real=True)
+    M, a, S, s, m = sp.symbols("M a S s m", real=True)
+    k1, k2, k3 = sp.symbols("k1 k2 k3")
+    T = sp.Function("T")(r)       # tortoise r*(r); only r* ' = varpi/Delta enters
+    P = sp.Function("P")(r)       # int a/Delta dr; only P' = a/Delta enters
+    Delta = r ** 2 - 2 * M * r + a ** 2
+    varpi = r ** 2 + a ** 2
+    tt = t - r + T                                       # ingoing Kerr time
+    tau = tt - r ** 2 / (r + S) + 4 * M * sp.log(S / (r + S))
+    rho = r / (1 + r / S)
+    pht = ph + P
+    g = Delta ** (-s) / r if rescale else sp.Integer(1)
+    Psi = g * sp.exp(k1 * tau + k2 * rho + k3 * th + sp.I * m * pht)
+    sn, cs = sp.sin(th), sp.cos(th)
+    L = (-(varpi ** 2 / Delta - a ** 2 * sn ** 2) * sp.diff(Psi, t, 2)
+         - 4 * M * a * r / Delta * sp.diff(Psi, t, ph)
+         - 2 * s * (r - M * (r ** 2 - a ** 2) / Delta + sp.I * a * cs) * sp.diff(Psi, t)
+         + Delta ** (-s) * sp.diff(Delta ** (s + 1) * sp.diff(Psi, r), r)
+         + sp.diff(sn * sp.diff(Psi, th), th) / sn
+         + (1 / sn ** 2 - a ** 2 / Delta) * sp.diff(Psi, ph, 2)
+         + 2 * s * (a * (r - M) / Delta + sp.I * cs / sn ** 2) * sp.diff(Psi, ph)
+         - (s ** 2 * cs ** 2 / sn ** 2 - s) * Psi)
+    E = L / Psi
+    E = E.subs({sp.Derivative(T, (r, 2)): sp.diff(varpi / Delta, r),
+                sp.Derivative(P, (r, 2)): sp.diff(a / Delta, r)})
+    E = E.subs({sp.Derivative(T, r): varpi / Delta, sp.Derivative(P, r): a / Delta})
+    E = E.subs({T: 0, P: 0, t: 0, ph: 0})
+    return sp.lambdify((k1, k2, k3, r, th, M, a, S, s, m), E, "mpmath")
+
+
+@pytest.fixture(scope="module")
+def op_phi():
+    return _operator(True)
+
+
+def _first_order(op, r, th, M, a, S, s, m):
+    """b, c, K, Bt, C, Ath, Bth of Sec. 2.3 from the operator, at (r, theta)."""
+    def coeffs(rr):
+        E = lambda k1, k2, k3: op(k1, k2, k3, rr, th, M, a, S, s, m)
+        c0 = E(0, 0, 0)
+        Att = (E(1, 0, 0) + E(-1, 0, 0) - 2 * c0) / 2
+        Bt = (E(1, 0, 0) - E(-1, 0, 0)) / 2
+        Arr = (E(0, 1, 0) + E(0, -1, 0) - 2 * c0) / 2
+        Br = (E(0, 1, 0) - E(0, -1, 0)) / 2
+        Atr = E(1, 1, 0) - c0 - Att - Bt - Arr - Br
+        Ahh = (E(0, 0, 1) + E(0, 0, -1) - 2 * c0) / 2
+        Bh = (E(0, 0, 1) - E(0, 0, -1)) / 2
+        D = -Att
+        return dict(Atr=Atr / D, Arr=Arr / D, Bt=Bt / D, Br=Br / D, C=c0 / D,
+                    Ath=Ahh / D, Bth=Bh / D)
+
+    def bfun(rr):
+        q = coeffs(rr)
+        return (-q["Atr"] + mp.sqrt(q["Atr"] ** 2 + 4 * q["Arr"])) / 2
+
+    q = coeffs(r)
+    b = bfun(r)
+    c = q["Atr"] + b
+    drho_dr = (S / (r + S)) ** 2
+    b_rho = mp.diff(lambda x: mp.re(bfun(x)), r) / drho_dr
+    K = q["Br"] - b * q["Bt"] - c * b_rho
+    return dict(b=b, c=c, K=K, Bt=q["Bt"], C=q["C"], Ath=q["Ath"], Bth=q["Bth"])
+
+
+def _compare(got, ref, scale, tol):
+    gotc = dict(b=got[0], K=got[1] + 1j * got[2], Bt=got[3] + 1j * got[4],
+                C=got[5] + 1j * got[6], Ath=got[7], Bth=got[8], c=got[9])
+    for k, v in gotc.items():
+        e = complex(ref[k])
+        assert abs(v - e) <= tol * max(scale, abs(e)), (k, v, e)
+
+
+@pytest.mark.parametrize("a,s,m", [(0.0, 0, 0), (0.0, -2, 0), (1.0, -2, 0), (0.7, -2, 2),
+                                   (0.5, -1, 1), (0.9, 2, -3), (1.0, 0, 1)])
+def test_hyperboloidal_coefficients_match_teukolsky_equation(op_phi, a, s, m):
+    """Eq. near_final's coefficients for Phi on the slices of Sec. 2.2, from
+    the horizon to far out, against the oracle's closed forms."""
+    mp.mp.dps = 40
+    M, S = 1.0, 20.0
+    rp = M + np.sqrt(max(M * M - a * a, 0.0))
+    rng = np.random.default_rng(7)
+    radii = [rp * (1 + 1e-6), rp * 1.01, 1.7 * rp, 4.0, 12.0, 60.0, 900.0, 5e4]
+    for r in radii:
+        th = float(rng.uniform(0.1, np.pi - 0.1))
+        rho = S * r / (r + S)
+        got = o.coeff_point_hyp(rho, th, M, a, S, s, m)
+        rr = mp.mpf(S) * mp.mpf(rho) / (mp.mpf(S) - mp.mpf(rho))    # r of the same rho
+        ref = _first_order(op_phi, rr, mp.mpf(th), M, a, S, s, m)
+        _compare(got, ref, 1e-3, 1e-9)
+
+
+def test_speeds_vanish_on_the_horizon_and_at_scri():
+    """b = 0 on the horizon (the outgoing speed), c = 0 at scri (the ingoing
+    one); both ends are outflow boundaries, so Psi rows upwind from the left
+    and pi rows from the right everywhere in between (Sec. 3.1.2)."""
+    M, S = 1.0, 20.0
+    for a in [0.0, 0.6, 1.0]:
+        rhop = o.horizon_rho(M, a, S)
+        for th in [0.3, 1.2, 2.9]:
+            ch = o.coeff_point_hyp(rhop, th, M, a, S, -2, 2)
+            cs = o.coeff_point_hyp(S, th, M, a, S, -2, 2)
+            assert abs(ch[0]) < 1e-14 and ch[9] > 0.1
+            assert cs[9] == 0.0 and cs[0] > 0.5
+            for rho in np.linspace(rhop, S, 97):
+                c = o.coeff_point_hyp(rho, th, M, a, S, -2, 2)
+                assert c[0] >= -1e-14 and c[9] >= 0.0
+                assert np.all(np.isfinite(c))
+
+
+def test_scri_values_are_the_limit(op_phi):
+    """The closed forms evaluated at rho = S (r infinite) equal the limit of the
+    operator's coefficients as r grows."""
+    mp.mp.dps = 40
+    M, S, a, s, m = 1.0, 20.0, 0.8, -2, 2
+    th = 1.1
+    got = o.coeff_point_hyp(S, th, M, a, S, s, m)
+    ref = _first_order(op_phi, mp.mpf(10) ** 14, mp.mpf(th), M, a, S, s, m)
+    _compare(got, ref, 1e-3, 1e-9)
+
+
+@pytest.mark.parametrize("a,s,m", [(0.0, 0, 0), (0.999, -2, 2), (0.5, -1, 3), (0.3, 2, -1)])
+def test_rescaled_field_in_rstar_matches_teukolsky_equation(a, s, m):
+    """field 1 in r*: Psi = Phi Delta^-s / r plugged into Eq. teuk0 (BL t,
+    tortoise r*); the coefficients of the Phi equation read off as above."""
+    mp.mp.dps = 40
+    t, r, th, ph = sp.symbols("t r theta phi", real=True)
+    k1, k2, k3 = sp.symbols("k1 k2 k3")
+    Rs = sp.Function("Rs")(r)
+    Pf = sp.Function("P")(r)
+    M = 1.0
+    Delta = r ** 2 - 2 * M * r + a ** 2
+    varpi = r ** 2 + a ** 2
+    g = Delta ** (-s) / r
+    Psi = g * sp.exp(k1 * t + k2 * Rs + k3 * th + sp.I * m * (ph + Pf))
+    sn, cs = sp.sin(th), sp.cos(th)
+    L = (-(varpi ** 2 / Delta - a ** 2 * sn ** 2) * sp.diff(Psi, t, 2)
+         - 4 * M * a * r / Delta * sp.diff(Psi, t, ph)
+         - 2 * s * (r - M * (r ** 2 - a ** 2) / Delta + sp.I * a * cs) * sp.diff(Psi, t)
+         + Delta ** (-s) * sp.diff(Delta ** (s + 1) * sp.diff(Psi, r), r)
+         + sp.diff(sn * sp.diff(Psi, th), th) / sn
+         + (1 / sn ** 2 - a ** 2 / Delta) * sp.diff(Psi, ph, 2)
+         + 2 * s * (a * (r - M) / Delta + sp.I * cs / sn ** 2) * sp.diff(Psi, ph)
+         - (s ** 2 * cs ** 2 / sn ** 2 - s) * Psi)
+    E = (L / Psi).subs({sp.Derivative(Rs, (r, 2)): sp.diff(varpi / Delta, r),
+                        sp.Derivative(Pf, (r, 2)): sp.diff(a / Delta, r)})
+    E = E.subs({sp.Derivative(Rs, r): varpi / Delta, sp.Derivative(Pf, r): a / Delta})
+    E = E.subs({Rs: 0, Pf: 0, t: 0, ph: 0})
+    op = sp.lambdify((k1, k2, k3, r, th), E, "mpmath")
+
+    def coeffs(rr, tt):
+        F = lambda x, y, z: op(x, y, z, rr, tt)
+        c0 = F(0, 0, 0)
+        Att = (F(1, 0, 0) + F(-1, 0, 0) - 2 * c0) / 2
+        D = -Att
+        q = dict(Bt=(F(1, 0, 0) - F(-1, 0, 0)) / 2 / D,
+                 Axx=(F(0, 1, 0) + F(0, -1, 0) - 2 * c0) / 2 / D,
+                 Bx=(F(0, 1, 0) - F(0, -1, 0)) / 2 / D,
+                 Atx=(F(1, 1, 0) - c0 - Att - (F(1, 0, 0) - F(-1, 0, 0)) / 2
+                      - (F(0, 1, 0) + F(0, -1, 0) - 2 * c0) / 2
+                      - (F(0, 1, 0) - F(0, -1, 0)) / 2) / D,
+                 Ath=(F(0, 0, 1) + F(0, 0, -1) - 2 * c0) / 2 / D,
+                 Bth=(F(0, 0, 1) - F(0, 0, -1)) / 2 / D, C=c0 / D)
+        return q
+
+    rp = M + np.sqrt(max(M * M - a * a, 0.0))
+    rng = np.random.default_rng(11)
+    for _ in range(6):
+        rv = rp + 10.0 ** rng.uniform(-1.0, 2.5)
+        tv = float(rng.uniform(0.1, np.pi - 0.1))
+        q = coeffs(mp.mpf(rv), mp.mpf(tv))
+        assert abs(q["Atx"]) < 1e-25
+        bfun = lambda x: mp.sqrt(mp.re(coeffs(x, mp.mpf(tv))["Axx"]))
+        b = bfun(mp.mpf(rv))
+        drs_dr = (rv * rv + a * a) / (rv * rv - 2 * M * rv + a * a)
+        b_star = mp.diff(bfun, mp.mpf(rv)) / drs_dr
+        K = q["Bx"] - b * b_star - b * q["Bt"]
+        ref = dict(b=b, c=b, K=K, Bt=q["Bt"], C=q["C"], Ath=q["Ath"], Bth=q["Bth"])
+        got = o.coeff_point(rv, tv, M, a, s, m, 1)
+        _compare(got, ref, 1e-3, 1e-10)
+
+
+@pytest.mark.parametrize("dir", [1, -1])
+def test_extrapolated_ghosts_keep_linear_weights_exact_to_degree_four(dir):
+    """bc 2 (the hyperboloidal grid's ghosts): quartic extrapolation through
+    the five edge nodes, so with the linear weights the WENO5 derivative is
+    exact for polynomials of degree <= 4 at every node, edges included; a
+    quintic is no longer exact at the edges."""
+    n, h = 30, 0.1
+    x = np.arange(n) * h
+    for deg in range(5):
+        f = (x - 1.1) ** deg
+        D = o.weno5_deriv_1d(f, h, dir, force_w=[0.1, 0.6, 0.3], bc=2)
+        ex = deg * (x - 1.1) ** (deg - 1) if deg else 0 * x
+        assert np.max(np.abs(D - ex)) < 1e-9 * max(1.0, np.max(np.abs(ex))), deg
+    f = (x - 1.1) ** 5
+    D = o.weno5_deriv_1d(f, h, dir, force_w=[0.1, 0.6, 0.3], bc=2)
+    ex = 5 * (x - 1.1) ** 4
+    assert np.max(np.abs(D[5:n - 5] - ex[5:n - 5])) < 1e-8
+    assert max(abs(D[0] - ex[0]), abs(D[-1] - ex[-1])) > 1e-4
+
+
+def test_price_tails_at_horizon_and_scri_on_the_hyperboloidal_grid():
+    """Schwarzschild, s = m = 0, l = 0 data: with the horizon and scri on the
+    grid, Price's law gives Phi ~ tau^-3 on the horizon and tau^-2 at scri
+    (rPsi ~ u^-(l+2) there); the local index p = tau dPhi/dtau / Phi."""
+    M, S, nr, nth = 1.0, 20.0, 512, 4
+    rhop = o.horizon_rho(M, 0.0, S)
+    g = o.grid(nr, nth, rhop, S, M, 0.0, 0, 0, coords=1, S=S)
+    co = o.coefficients(g)
+    h = (S - rhop) / (nr - 1)
+    dt = 0.5 * h / np.max(np.maximum(co[0], co[9]))
+    rho = rhop + h * np.arange(nr)
+    u = np.zeros((4, nth, nr))
+    u[0] = np.exp(-((rho - 5.0) / 0.5) ** 2)[None, :]
+    chunk = int(round(5.0 / dt))
+    ts, hor, scri = [], [], []
+    t = 0.0
+    while t < 400.0:
+        u = o.rk3_step(g, co, dt, u, chunk)
+        t += chunk * dt
+        ts.append(t)
+        hor.append(u[0, 0, 0])
+        scri.append(u[0, 0, -1])
+    ts, hor, scri = np.array(ts), np.array(hor), np.array(scri)
+
+    def index(f):
+        return ts[1:-1] * (f[2:] - f[:-2]) / (ts[2:] - ts[:-2]) / f[1:-1]
+
+    late = ts[1:-1] > 300.0
+    assert np.all(np.abs(index(hor)[late] + 3.0) < 0.1), index(hor)[late]
+    assert np.all(np.abs(index(scri)[late] + 2.0) < 0.15), index(scri)[late]

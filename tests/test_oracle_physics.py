@@ -162,17 +162,20 @@ def test_theta_weno_option_on_spin_weighted_harmonics(case, a):
     assert errs[-1] < 1e-5 * abs(lam) + 1e-9
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
-def test_assembly_matches_printed_real_matrices(scheme):
-    """F = -(M du/dr* + L u + A u) with M, A, L exactly as printed in Sec. 2.3,
+@pytest.mark.parametrize("scheme,coords", [(0, 0), (1, 0), (0, 1)])
+def test_assembly_matches_printed_real_matrices(scheme, coords):
+    """F = -(M du/dx + L u + A u) with M, A, L exactly as printed in Sec. 2.3,
     using m31 = -Re K, m32 = Im K, a31 = -Re C, a32 = Im C, a33 = -Re Bt,
-    a34 = Im Bt, l31 = -(Ath d2/dth2 + Bth d/dth), on data linear in r*
-    (where every WENO derivative is exact) times sY_lm(theta)."""
+    a34 = Im Bt, l31 = -(Ath d2/dth2 + Bth d/dth), on data linear in x = r*
+    or rho (where every WENO derivative is exact, the hyperboloidal grid's
+    extrapolated ghosts included) times sY_lm(theta). On the hyperboloidal
+    slices the pi rows' diagonal entry is -c, c = Atr + b (-b when Atr = 0)."""
     s, l, m, a, M = -2, 3, 2, 0.7, 1.0
     nr, nth = 64, 128
-    g = o.grid(nr, nth, 5.0, 15.0, M, a, s, m, scheme=scheme)
+    x0, x1 = (5.0, 15.0) if coords == 0 else (2.5, 20.0)
+    g = o.grid(nr, nth, x0, x1, M, a, s, m, scheme=scheme, coords=coords, S=20.0)
     co = o.coefficients(g)
-    rs = I.rstar_nodes(nr, 5.0, 15.0)
+    rs = I.rstar_nodes(nr, x0, x1)
     th = I.theta_nodes(nth)
     Y = I.swsh(s, l, m, th)[:, None]
     al, be, ga, de = 0.3 - 0.2j, 0.7 + 0.4j, -0.5 + 0.1j, 0.2 - 0.9j
@@ -182,7 +185,9 @@ def test_assembly_matches_printed_real_matrices(scheme):
     F = o.rhs(g, co, u)
     du = np.stack([(be * Y).real + 0 * rs, (be * Y).imag + 0 * rs,
                    (de * Y).real + 0 * rs, (de * Y).imag + 0 * rs])
-    b, Kr, Ki, Btr, Bti, Cr, Ci, Ath, Bth = co
+    b, Kr, Ki, Btr, Bti, Cr, Ci, Ath, Bth, c = co
+    if coords == 0:
+        np.testing.assert_array_equal(c, b)
     lam = -(l - s) * (l + s + 1)
     cth = np.cos(th)[:, None]
     sth = np.sin(th)[:, None]
@@ -190,7 +195,7 @@ def test_assembly_matches_printed_real_matrices(scheme):
     Lpsi = -(Ath * ang) * u[0:2]                          # l31 acting on Psi_R, Psi_I
     m31, m32, a31, a32, a33, a34 = -Kr, Ki, -Cr, Ci, -Btr, Bti
     z = np.zeros_like(b)
-    Mm = [[b, z, z, z], [z, b, z, z], [m31, m32, -b, z], [-m32, m31, z, -b]]
+    Mm = [[b, z, z, z], [z, b, z, z], [m31, m32, -c, z], [-m32, m31, z, -c]]
     Am = [[z, z, -1 + z, z], [z, z, z, -1 + z], [a31, a32, a33, a34], [-a32, a31, -a34, a33]]
     exp_ = np.zeros_like(u)
     for row in range(4):
@@ -198,7 +203,7 @@ def test_assembly_matches_printed_real_matrices(scheme):
         if row >= 2:
             acc = acc + Lpsi[row - 2]
         exp_[row] = -acc
-    sl = (slice(None), slice(5, nr - 5))
+    sl = (slice(None), slice(5, nr - 5) if coords == 0 else slice(None))
     for row in range(4):
         scale = np.max(np.abs(exp_[row][sl]))
         err = np.max(np.abs(F[row][sl] - exp_[row][sl]))
