@@ -2,21 +2,26 @@
  * teuk.h -- C ABI of the GB300 (sm_103a) mixed-precision WENO5 Teukolsky solver.
  *
  * The library advances one azimuthal m-mode of the Teukolsky master equation
- * (arXiv 2010.04760, Eq. teuk0) on a 2+1-D (r*, theta) grid. Each Runge-Kutta
- * stage evaluates the first-order system du/dt = -(M du/dr* + L u + A u)
- * (Sec. 2.3, Eq. evln) with the WENO5 (Jiang-Shu) derivative in r*
- * (Sec. 3.1.2), the nonlinear weights computed in a reduced precision
- * (Sec. 3.1.3), fourth-order centred differences in theta (Sec. 3.1: "standard
- * centered differencing"), and the SSP-RK(3,3) update (Sec. 3.2).
+ * (arXiv 2010.04760, Eq. teuk0) on a 2+1-D (x, theta) grid, x the tortoise
+ * r* or the hyperboloidal rho of Sec. 2.2. Each Runge-Kutta stage evaluates
+ * the first-order system du/dt = -(M du/dx + L u + A u) (Sec. 2.3, Eq. evln)
+ * with the WENO5 (Jiang-Shu) derivative in x (Sec. 3.1.2), the nonlinear
+ * weights computed in a reduced precision (Sec. 3.1.3), fourth-order centred
+ * differences in theta (Sec. 3.1: "standard centered differencing"), and the
+ * SSP-RK(3,3) update (Sec. 3.2).
  *
  * Conventions shared by every call
- *  - State vector u = {Psi_R, Psi_I, pi_R, pi_I} (Sec. 2.3). In memory it is
- *    four planes, component-major: u[c][j][i], c = 0..3, j = theta row
- *    0..ntheta-1, i = r* node 0..nr-1 (fastest). 4*ntheta*nr doubles.
- *  - Grid: r*_i = rstar_min + i h, h = (rstar_max - rstar_min)/(nr - 1);
+ *  - State vector u = {Psi_R, Psi_I, pi_R, pi_I} (Sec. 2.3), Psi standing for
+ *    the evolved field (Psi, or Phi = r Delta^s Psi, see teuk_field). In
+ *    memory it is four planes, component-major: u[c][j][i], c = 0..3,
+ *    j = theta row 0..ntheta-1, i = radial node 0..nr-1 (fastest).
+ *    4*ntheta*nr doubles.
+ *  - Grid: x_i = rstar_min + i h, h = (rstar_max - rstar_min)/(nr - 1), the
+ *    two bounds holding the range of r* or of rho (teuk_coords);
  *    theta_j = (j + 1/2) pi / ntheta (cell centred, never on a pole).
- *  - Time is Boyer-Lindquist t; the azimuth is the ingoing phi~ (Sec. 2.2),
- *    Psi = exp(i m phi~) psi(t, r*, theta); pi = psi_t + b psi_*.
+ *  - In r*, time is Boyer-Lindquist t; on the hyperboloidal slices it is tau.
+ *    The azimuth is the ingoing phi~ (Sec. 2.2) either way,
+ *    Psi = exp(i m phi~) psi(t, x, theta); pi = psi_t + b psi_x.
  *  - Host pointers are read or written synchronously and stay owned by the
  *    caller. Device pointers ("_dev") are caller-owned device memory on the
  *    current CUDA device. Handles own their device memory.
@@ -65,7 +70,7 @@ typedef enum {
                                   stays fourth-order centred */
 } teuk_theta_mode;
 
-/* Discretisation in r* (Sec. 3.1). */
+/* Discretisation of the radial derivative (Sec. 3.1). */
 typedef enum {
     TEUK_SCHEME_WENO5 = 0,    /* fifth-order WENO (Jiang-Shu), the method       */
     TEUK_SCHEME_FD6_KO8 = 1   /* the paper's comparison scheme (Sec. 3.1.1):
@@ -82,13 +87,44 @@ typedef enum {
                              low-storage (two-register) evaluation            */
 } teuk_rk;
 
+/* Radial coordinate and slicing (Sec. 2.2). */
+typedef enum {
+    TEUK_COORDS_RSTAR = 0,         /* Boyer-Lindquist t, tortoise r*; the
+                                      radial ghosts copy the edge value       */
+    TEUK_COORDS_HYPERBOLOIDAL = 1  /* the paper's horizon-penetrating,
+                                      compactified slices:
+                                      tau = t~ - r^2/(r+S) + 4M ln(S/(r+S)),
+                                      rho = r/(1 + r/S), t~ the ingoing Kerr
+                                      time; the grid lies between the outer
+                                      horizon rho_+ and scri (rho = S), both
+                                      outflow boundaries, and the radial
+                                      ghosts extrapolate the quartic through
+                                      the five edge nodes. The pi rows move
+                                      with their own speed -c (M33 = -c,
+                                      c = Atr + b). Requires TEUK_FIELD_PHI,
+                                      TEUK_SCHEME_WENO5 and
+                                      TEUK_THETA_CENTERED4; not in batches.   */
+} teuk_coords;
+
+/* Evolved field. */
+typedef enum {
+    TEUK_FIELD_PSI = 0,   /* the Teukolsky function Psi of Eq. teuk0            */
+    TEUK_FIELD_PHI = 1    /* Phi = r Delta^s Psi (Sec. 4's Phi = (r/Delta^2) Psi
+                             at s = -2): finite on the horizon and at scri, and
+                             O(1) at large r in r* as well                      */
+} teuk_field;
+
 /* Problem statement (Sec. 2.1-2.3, Sec. 4): grid, domain, black hole, mode.
  * Valid ranges: nr >= 7, ntheta >= 5, rstar_max > rstar_min, M > 0,
  * 0 <= |a| <= M, s in {-2..2}, |m| <= 64, eps in [1e-60, 1],
- * dt > 0, or dt == 0 with cfl in (0, 1] (dt from the stability rule below). */
+ * dt > 0, or dt == 0 with cfl in (0, 1] (dt from the stability rule below).
+ * TEUK_COORDS_HYPERBOLOIDAL: hyp_S in [M, 1e6 M], and
+ * rho_+ <= rstar_min < rstar_max <= S (rho_+ = r_+ S/(r_+ + S), r_+ = M +
+ * sqrt(M^2 - a^2); a bound within 1e-12 relative of rho_+ or S counts as it);
+ * rstar_min == rstar_max == 0 selects the whole range [rho_+, S]. */
 typedef struct {
-    int nr, ntheta;                 /* grid nodes in r* and theta            */
-    double rstar_min, rstar_max;    /* r* domain in units of M               */
+    int nr, ntheta;                 /* grid nodes in x and theta             */
+    double rstar_min, rstar_max;    /* x domain (r* or rho) in units of M    */
     double M, a;                    /* mass and spin                         */
     int s, m;                       /* spin weight, azimuthal number         */
     double cfl;                     /* Courant factor when dt == 0           */
@@ -99,6 +135,9 @@ typedef struct {
     int rk;                         /* teuk_rk                               */
     int scheme;                     /* teuk_scheme                           */
     double ko_sigma;                /* Kreiss-Oliger sigma (paper: 0.01)     */
+    int coords;                     /* teuk_coords                           */
+    int field;                      /* teuk_field                            */
+    double hyp_S;                   /* slice parameter S (paper: ~20 M)      */
 } teuk_params;
 
 typedef struct teuk_handle teuk_handle;
@@ -118,17 +157,18 @@ const char* teuk_last_error(void);
 teuk_status teuk_check_params(const teuk_params* p);
 
 /* Time step of the stability rule used when p->dt == 0:
- *   dt = cfl / max_ij [ b/h + sqrt(kappa) ],
+ *   dt = cfl / max_ij [ max(|b|, |c|)/h + sqrt(kappa) ],
  *   kappa = Ath (16/3)/dtheta^2 + |Bth| (3/2)/dtheta + |C|,
- * a bound of the largest frequency of the r* upwind part (b/h, Sec. 3.2
- * forward-Euler limit) plus the theta part of the second-order operator;
- * times 2.8 for TEUK_RK_SSP104 (the smaller of its real- and imaginary-axis
- * stability extents relative to SSP-RK(3,3)). If p->dt > 0 it is returned
- * unchanged. */
+ * a bound of the largest frequency of the radial upwind part (the larger of
+ * the two characteristic speeds over h, Sec. 3.2 forward-Euler limit; c = b
+ * in r*) plus the theta part of the second-order operator; times 2.8 for
+ * TEUK_RK_SSP104 (the smaller of its real- and imaginary-axis stability
+ * extents relative to SSP-RK(3,3)). If p->dt > 0 it is returned unchanged. */
 teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out);
 
 /* Number of doubles in the kernel coefficient array of p (11 planes of
- * ntheta*nr, 12 with TEUK_THETA_WENO5). 0 if p is invalid. */
+ * ntheta*nr, 12 with TEUK_THETA_WENO5, 13 with TEUK_COORDS_HYPERBOLOIDAL).
+ * 0 if p is invalid. */
 size_t teuk_coeff_count(const teuk_params* p);
 
 /* Kernel coefficient array for time step dt, written to host memory
@@ -137,7 +177,9 @@ size_t teuk_coeff_count(const teuk_params* p);
  * integrator (dt for SSP-RK(3,3), dt/6 for SSP-RK(10,4)) and by 1/(6h),
  * 1/(12 dtheta^k) for the stencil normalisations, with the theta pole parity
  * folded into the theta-stencil planes. Built on the host in binary64; r(r*)
- * from the tortoise relation of Sec. 2.2. */
+ * from the tortoise relation of Sec. 2.2; on the hyperboloidal slices the
+ * coefficients of Eq. near_final for Phi, derived from Eq. teuk0 (they are
+ * not printed in the paper). */
 teuk_status teuk_build_coefficients(const teuk_params* p, double dt,
                                     double* coef_host);
 
@@ -156,7 +198,7 @@ teuk_status teuk_fp64_fma_rate(void* stream, double* fma_per_s);
  *   stage 2: u_out = 3/4 u_n + 1/4 (u_prev + h F(u_prev))   (SSP-RK(3,3) only)
  *   stage 3: u_out = 1/3 u_n + 2/3 (u_prev + h F(u_prev))   (SSP-RK(3,3) only)
  *   stage 0: u_out = h F(u_prev)    (the operator alone, for checks)
- * F is the right-hand side of Eq. evln with the WENO5 r* derivative.
+ * F is the right-hand side of Eq. evln with the WENO5 radial derivative.
  * dt must be the step coef_dev was built for (teuk_build_coefficients).
  * coef_dev: teuk_coeff_count(p) doubles. u_n (read for stages 2, 3; may be
  * NULL otherwise), u_prev, u_out: 4*ntheta*nr doubles. u_out must not alias
@@ -223,7 +265,8 @@ teuk_status teuk_set_initial(teuk_handle* h, const double* psi,
 
 /* Initial data of the paper's kind (Sec. 4: a Gaussian wave packet times
  * spin-weighted harmonics), built on the host and copied in:
- *   Psi(r*, theta) = sum_{k<nl} c_k exp(-(r* - rc)^2 / (2 width^2)) sY_{l_k m}(theta),
+ *   Psi(x, theta) = sum_{k<nl} c_k exp(-(x - rc)^2 / (2 width^2)) sY_{l_k m}(theta),
+ * x the radial coordinate (r* or rho),
  *   l_k = max(|s|, |m|) + k,  pi = 0,  t = 0,
  * sY_lm by the Goldberg et al. (1967) sum formula at phi = 0. coeffs: 2*nl
  * doubles (re, im) per term; if coeffs is NULL, c_k = A_k exp(i phi_k) with
@@ -239,14 +282,19 @@ teuk_status teuk_set_gaussian(teuk_handle* h, double rc, double width, const dou
 teuk_status teuk_set_state(teuk_handle* h, const double* u_host, double t);
 teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out);
 
-/* Advance nsteps SSP-RK(3,3) steps (3 fused stage launches each, replayed
- * from a captured CUDA graph). Asynchronous on the handle's stream. */
+/* Advance nsteps steps of p's integrator (3 fused stage launches each for
+ * SSP-RK(3,3), 11 for SSP-RK(10,4)), replayed from a captured CUDA graph.
+ * Asynchronous on the handle's stream. */
 teuk_status teuk_step(teuk_handle* h, int64_t nsteps);
 
-/* Observation (Sec. 4): wave[2*ntheta] = Psi (re, im) along theta at the r*
- * node nearest rstar_ext; horizon[6*ntheta] = for each theta row, Psi, pi
- * and dPsi/dr* (one-sided, second order) at the innermost node i = 0, each
- * as (re, im). Either output may be NULL. t_out (may be NULL) = current t.
+/* Observation (Sec. 4): wave[2*ntheta] = Psi (re, im) along theta at the
+ * radial node nearest rstar_ext (an r* or a rho: rho = S reads the field at
+ * scri); horizon[6*ntheta] = for each theta row, Psi, pi and dPsi/dx
+ * (one-sided, second order) at the innermost node i = 0, each as (re, im).
+ * On the hyperboloidal slices with rstar_min = rho_+, node 0 is the horizon,
+ * and these are Phi, pi and the radial derivative whose late-time behaviour
+ * Sec. 4 compares with Aretakis' laws. Either output may be NULL. t_out (may
+ * be NULL) = current t (tau on the hyperboloidal slices).
  * Synchronises the handle's stream. Returns TEUK_ERR_NONFINITE if a gathered
  * value is not finite. */
 teuk_status teuk_observe(teuk_handle* h, double rstar_ext, double* wave,

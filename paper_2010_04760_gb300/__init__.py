@@ -23,6 +23,8 @@ TEUK_W_FP64, TEUK_W_FP32, TEUK_W_FP16, TEUK_W_BF16 = range(4)
 TEUK_THETA_CENTERED4, TEUK_THETA_WENO5 = 0, 1
 TEUK_RK_SSP33, TEUK_RK_SSP104 = 0, 1
 TEUK_SCHEME_WENO5, TEUK_SCHEME_FD6_KO8 = 0, 1
+TEUK_COORDS_RSTAR, TEUK_COORDS_HYPERBOLOIDAL = 0, 1
+TEUK_FIELD_PSI, TEUK_FIELD_PHI = 0, 1
 WPREC = {"fp64": TEUK_W_FP64, "fp32": TEUK_W_FP32, "fp16": TEUK_W_FP16, "bf16": TEUK_W_BF16}
 COEF_PLANES = 11
 
@@ -41,7 +43,9 @@ class teuk_params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("eps", ctypes.c_double), ("wprec", ctypes.c_int),
                 ("theta_mode", ctypes.c_int), ("rk", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("ko_sigma", ctypes.c_double)]
+                ("scheme", ctypes.c_int), ("ko_sigma", ctypes.c_double),
+                ("coords", ctypes.c_int), ("field", ctypes.c_int),
+                ("hyp_S", ctypes.c_double)]
 
 
 _lib = None
@@ -135,17 +139,35 @@ def _host(a):
     return a, a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_params(nr, ntheta, rstar_min=-100.0, rstar_max=300.0, M=1.0, a=0.0, s=0, m=0,
+def horizon_rho(M, a, S):
+    """rho of the outer horizon on the hyperboloidal slices, r_+ S/(r_+ + S)."""
+    rp = M + (max(M * M - a * a, 0.0)) ** 0.5
+    return rp * S / (rp + S)
+
+
+def make_params(nr, ntheta, rstar_min=None, rstar_max=None, M=1.0, a=0.0, s=0, m=0,
                 cfl=0.5, dt=0.0, eps=1e-6, wprec="fp64", theta_mode=TEUK_THETA_CENTERED4,
-                rk=TEUK_RK_SSP33, scheme=TEUK_SCHEME_WENO5, ko_sigma=0.01):
+                rk=TEUK_RK_SSP33, scheme=TEUK_SCHEME_WENO5, ko_sigma=0.01,
+                coords=TEUK_COORDS_RSTAR, field=None, hyp_S=20.0):
+    """teuk_params with defaults: r* in [-100, 300] M; on the hyperboloidal
+    slices the whole range [rho_+, S] and the field Phi."""
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
+    hyp = coords == TEUK_COORDS_HYPERBOLOIDAL
+    if rstar_min is None:
+        rstar_min = horizon_rho(M, a, hyp_S) if hyp else -100.0
+    if rstar_max is None:
+        rstar_max = hyp_S if hyp else 300.0
+    if field is None:
+        field = TEUK_FIELD_PHI if hyp else TEUK_FIELD_PSI
     return teuk_params(nr, ntheta, rstar_min, rstar_max, M, a, s, m, cfl, dt, eps, w, theta_mode,
-                       rk, scheme, ko_sigma)
+                       rk, scheme, ko_sigma, coords, field, hyp_S)
 
 
 def params_from_workload(wl, **over):
     kw = dict(nr=wl.nr, ntheta=wl.nth, rstar_min=wl.rs_min, rstar_max=wl.rs_max, M=wl.M, a=wl.a,
-              s=wl.s, m=wl.m, cfl=wl.cfl, eps=wl.eps, wprec=wl.wprec)
+              s=wl.s, m=wl.m, cfl=wl.cfl, eps=wl.eps, wprec=wl.wprec,
+              coords=getattr(wl, "coords", TEUK_COORDS_RSTAR),
+              field=getattr(wl, "field", None), hyp_S=getattr(wl, "S", 20.0))
     kw.update(over)
     return make_params(**kw)
 

@@ -313,6 +313,8 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
             return fail(TEUK_ERR_ARG, "all members need the same wprec and theta_mode");
         if (ps[k].rk != TEUK_RK_SSP33 || ps[k].scheme != TEUK_SCHEME_WENO5)
             return fail(TEUK_ERR_ARG, "batched evolutions use WENO5 and SSP-RK(3,3)");
+        if (ps[k].coords != TEUK_COORDS_RSTAR)
+            return fail(TEUK_ERR_ARG, "batched evolutions use r* coordinates");
     }
     teuk_batch* b = new teuk_batch();
     b->n = n;
@@ -326,7 +328,7 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
         teuk_status st = teuk_stable_dt(&ps[k], &b->dt[k]);
         if (st != TEUK_OK) { delete b; return st; }
         b->off[k] = total;
-        total += (((12 + coef_planes(ps[k].theta_mode)) * b->plane(k) + 31) / 32) * 32;  // aligned
+        total += (((12 + coef_planes(ps[k])) * b->plane(k) + 31) / 32) * 32;  // aligned
         max_plane = std::max(max_plane, b->plane(k));
     }
     int dev = 0;
@@ -342,12 +344,13 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->pool, total * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&b->desc, batch_desc_bytes(n));
-    const int planes = coef_planes(ps[0].theta_mode);
-    std::vector<double> host((size_t)planes * max_plane);
+    int max_planes = 0;
+    for (int k = 0; k < n; ++k) max_planes = std::max(max_planes, coef_planes(ps[k]));
+    std::vector<double> host((size_t)max_planes * max_plane);
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
         teuk_status st = teuk_build_coefficients(&ps[k], b->dt[k], host.data());
         if (st != TEUK_OK) { teuk_batch_destroy(b); return st; }
-        e = cudaMemcpyAsync(b->coef(k), host.data(), planes * b->plane(k) * sizeof(double),
+        e = cudaMemcpyAsync(b->coef(k), host.data(), coef_planes(ps[k]) * b->plane(k) * sizeof(double),
                             cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host buffer is reused
     }
@@ -482,7 +485,7 @@ teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
     st = teuk_stable_dt(p, &h->dt);
     if (st != TEUK_OK) { delete h; return st; }
     const size_t n = h->plane();
-    std::vector<double> coef((size_t)coef_planes(p->theta_mode) * n);
+    std::vector<double> coef((size_t)coef_planes(*p) * n);
     st = teuk_build_coefficients(p, h->dt, coef.data());
     if (st != TEUK_OK) { delete h; return st; }
     cudaError_t e = cudaSuccess;

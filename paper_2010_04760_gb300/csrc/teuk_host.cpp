@@ -83,6 +83,11 @@ double r_of_rstar(double rstar, double M, double a, double* x_out) {
 //   Bt = [-2 s (r Delta - M (r^2-a^2)) - i (4 M a m r + 2 s a Delta cos)]/Sigma^2,
 //   C  = [Delta (s - (m + s cos)^2/sin^2) + 4 i s m a (r-M)]/Sigma^2,
 //   Ath = Delta/Sigma^2, Bth = Delta cot/Sigma^2.
+// For the field Phi = r Delta^s Psi (TEUK_FIELD_PHI), Psi = Phi Delta^-s / r
+// substituted into the same equation changes only B* and C:
+//   Re B* = -[2 a^2 Delta / r + 2 s (r-M) varpi]/Sigma^2,
+//   C    += [Delta (2a^2/r^2 - 2(1+s) M/r) - 2 i m a (2 s (r-M) + Delta/r)]/Sigma^2,
+// so that Im C = -2 m a Delta / (r Sigma^2).
 PointCoef point_coefficients(double rstar, double theta, const teuk_params& p) {
     double x;
     const double r = r_of_rstar(rstar, p.M, p.a, &x);
@@ -110,11 +115,85 @@ PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_par
     const double mc = m + s * cs;
     c.Cr = Delta * (s - mc * mc / (sn * sn)) * inv;
     c.Ci = 4.0 * s * m * a * (r - M) * inv;
-    c.Kr = Bs_r - b * bstar - b * c.Btr;
+    double Bsr = Bs_r;
+    if (p.field == TEUK_FIELD_PHI) {
+        Bsr = -(2.0 * a * a * Delta / r + 2.0 * s * (r - M) * varpi) * inv;
+        c.Cr += Delta * (2.0 * a * a / (r * r) - 2.0 * (1.0 + s) * M / r) * inv;
+        c.Ci = -2.0 * m * a * Delta / r * inv;
+    }
+    c.Kr = Bsr - b * bstar - b * c.Btr;
     c.Ki = Bs_i - b * c.Bti;
     c.Ath = Delta * inv;
     c.Bth = Delta * (cs / sn) * inv;
+    c.c = b;
     return c;
+}
+
+// Hyperboloidal slices (Sec. 2.2) for Phi = r Delta^s Psi: Eq. teuk0 under
+// tau = t + T(r), T' = varpi/Delta - H', H' = 2 - W^2 + 4MW/S,
+// rho = r/(1 + r/S), rho' = W^2, W = S/(r+S), and phi~ = phi + int a/Delta,
+// divided by D = -A^tautau. Every quantity is written in rho, W = 1 - rho/S
+// and x = 1/r = 1/rho - 1/S, finite from the horizon to scri:
+//   delta = Delta x^2 = 1 - x (2M - a^2 x),  w = varpi x^2 = 1 + a^2 x^2,
+//   sig = Sigma x^2 = sqrt(w^2 - a^2 x^2 delta sin^2),
+//   G = (2 varpi - Delta H') = rho (rho + 4M + 8M^2/S - 2MW + a^2 x (W - 4M/S)),
+//   E = Sigma + varpi - Delta H' = G - a^2 delta sin^2/(sig + w),
+//   D = H' G - a^2 sin^2.
+// The outgoing and ingoing speeds are b = rho^2 delta/E and c = W^2 E/D (the
+// roots of the characteristic quadratic, whose discriminant is 4 W^4 Sigma^2);
+// with pi = Phi_tau + b Phi_rho,
+//   pi_tau = c pi_rho + K Phi_rho + Ath Phi_thth + Bth Phi_th + Bt pi + C Phi,
+//   K = B^rho/D - b Bt - c db/drho,  Ath = 1/D,  Bth = cot/D,
+//   D Bt = 2 s rho (4M/S - W) - 2(1+s) M H' + 2a^2 x (H' - 1)
+//          - 2 delta rho^2 (W - 2M/S)/S + i (2 m a (1 - H') - 2 s a cos),
+//   B^rho = 2 i m a W^2 - 2 W rho ((s+1) - W - rho x (2M - a^2 x)/S)
+//           + 2 W^2 (M (1+s) - a^2 x),
+//   D C = s - (m + s cos)^2/sin^2 - 2(s+1) M x + 2a^2 x^2 - 2 i m a x.
+// db/drho is differentiated by hand from b = rho^2 delta / E.
+PointCoef point_coefficients_hyp(double rho, double theta, const teuk_params& p) {
+    const double M = p.M, a = p.a, s = p.s, m = p.m, S = p.hyp_S;
+    const double a2 = a * a;
+    const double sn = std::sin(theta), cs = std::cos(theta), sn2 = sn * sn;
+    const double x = 1.0 / rho - 1.0 / S, x_r = -1.0 / (rho * rho);
+    const double W = 1.0 - rho / S;
+    const double delta = 1.0 - x * (2.0 * M - a2 * x), delta_r = (2.0 * a2 * x - 2.0 * M) * x_r;
+    const double w = 1.0 + a2 * x * x, w_r = 2.0 * a2 * x * x_r;
+    const double sig2 = w * w - a2 * x * x * delta * sn2;
+    const double sig = std::sqrt(sig2);
+    const double sig_r = (2.0 * w * w_r - a2 * sn2 * (2.0 * x * x_r * delta + x * x * delta_r)) /
+                         (2.0 * sig);
+    const double Hp = 2.0 - W * W + 4.0 * M * W / S;
+    const double inner = rho + 4.0 * M + 8.0 * M * M / S - 2.0 * M * W + a2 * x * (W - 4.0 * M / S);
+    const double G = rho * inner;
+    const double G_r = inner + rho * (1.0 + 2.0 * M / S + a2 * x_r * (W - 4.0 * M / S) - a2 * x / S);
+    const double den = sig + w;
+    const double E = G - a2 * delta * sn2 / den;
+    const double E_r = G_r - a2 * sn2 * (delta_r * den - delta * (sig_r + w_r)) / (den * den);
+    const double D = Hp * G - a2 * sn2;
+    const double invD = 1.0 / D;
+    PointCoef c;
+    c.b = rho * rho * delta / E;
+    c.c = W * W * E * invD;
+    const double b_r = (2.0 * rho * delta + rho * rho * delta_r) / E - c.b * E_r / E;
+    c.Btr = (2.0 * s * rho * (4.0 * M / S - W) - 2.0 * (1.0 + s) * M * Hp + 2.0 * a2 * x * (Hp - 1.0)
+             - 2.0 * delta * rho * rho * (W - 2.0 * M / S) / S) * invD;
+    c.Bti = (2.0 * m * a * (1.0 - Hp) - 2.0 * s * a * cs) * invD;
+    const double Brr = (-2.0 * W * rho * ((s + 1.0) - W - rho * x * (2.0 * M - a2 * x) / S)
+                        + 2.0 * W * W * (M * (1.0 + s) - a2 * x)) * invD;
+    const double Bri = 2.0 * m * a * W * W * invD;
+    const double mc = m + s * cs;
+    c.Cr = (s - mc * mc / sn2 - 2.0 * (s + 1.0) * M * x + 2.0 * a2 * x * x) * invD;
+    c.Ci = -2.0 * m * a * x * invD;
+    c.Kr = Brr - c.b * c.Btr - c.c * b_r;
+    c.Ki = Bri - c.b * c.Bti;
+    c.Ath = invD;
+    c.Bth = (cs / sn) * invD;
+    return c;
+}
+
+double horizon_rho(double M, double a, double S) {
+    const double rp = M + std::sqrt(std::fmax(M * M - a * a, 0.0));
+    return rp * S / (rp + S);
 }
 
 // Spin-weighted spherical harmonic sY_lm(theta, phi = 0), Goldberg et al.
@@ -146,12 +225,25 @@ uint64_t splitmix64(uint64_t& state) {
     return z ^ (z >> 31);
 }
 
-// r and r - r_+ at every r* node.
+// Per radial node: r and r - r_+ at every r* node; rho itself on the
+// hyperboloidal grid (kept in r, x unused).
 static void radial_nodes(const teuk_params& p, std::vector<double>& r, std::vector<double>& x) {
     const double h = (p.rstar_max - p.rstar_min) / (p.nr - 1);
     r.resize(p.nr);
     x.resize(p.nr);
-    for (int i = 0; i < p.nr; ++i) r[i] = r_of_rstar(p.rstar_min + i * h, p.M, p.a, &x[i]);
+    for (int i = 0; i < p.nr; ++i) {
+        if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) {
+            r[i] = p.rstar_min + i * h;
+            x[i] = 0.0;
+        } else {
+            r[i] = r_of_rstar(p.rstar_min + i * h, p.M, p.a, &x[i]);
+        }
+    }
+}
+
+static PointCoef node_coefficients(double r, double x, double theta, const teuk_params& p) {
+    return p.coords == TEUK_COORDS_HYPERBOLOIDAL ? point_coefficients_hyp(r, theta, p)
+                                                 : point_coefficients_rx(r, x, theta, p);
 }
 
 // Runs body(j0, j1) over theta-row ranges on up to hardware_concurrency threads.
@@ -210,11 +302,30 @@ teuk_status teuk_check_params(const teuk_params* p) {
     if (p->rk != TEUK_RK_SSP33 && p->rk != TEUK_RK_SSP104)
         return fail(TEUK_ERR_ARG, "unknown time integrator");
     if (p->scheme != TEUK_SCHEME_WENO5 && p->scheme != TEUK_SCHEME_FD6_KO8)
-        return fail(TEUK_ERR_ARG, "unknown r* scheme");
+        return fail(TEUK_ERR_ARG, "unknown radial scheme");
     if (p->scheme == TEUK_SCHEME_FD6_KO8 && p->theta_mode != TEUK_THETA_CENTERED4)
         return fail(TEUK_ERR_ARG, "the FD6+KO8 scheme uses centred theta differences");
     if (p->scheme == TEUK_SCHEME_FD6_KO8 && !(p->ko_sigma >= 0.0 && p->ko_sigma <= 1.0))
         return fail(TEUK_ERR_ARG, "ko_sigma must be in [0, 1]");
+    if (p->field != TEUK_FIELD_PSI && p->field != TEUK_FIELD_PHI)
+        return fail(TEUK_ERR_ARG, "unknown field");
+    if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) {
+        if (p->field != TEUK_FIELD_PHI)
+            return fail(TEUK_ERR_ARG, "the hyperboloidal slices evolve Phi (TEUK_FIELD_PHI)");
+        if (p->scheme != TEUK_SCHEME_WENO5)
+            return fail(TEUK_ERR_ARG, "the hyperboloidal slices use the WENO5 scheme");
+        if (p->theta_mode != TEUK_THETA_CENTERED4)
+            return fail(TEUK_ERR_ARG, "the hyperboloidal slices use centred theta differences");
+        if (!(p->hyp_S >= p->M && p->hyp_S <= 1e6 * p->M))
+            return fail(TEUK_ERR_ARG, "hyp_S must be in [M, 1e6 M]");
+        const double rhop = horizon_rho(p->M, p->a, p->hyp_S);
+        if (p->rstar_min < rhop * (1.0 - 1e-12))
+            return fail(TEUK_ERR_ARG, "rho_min below the horizon rho_+");
+        if (p->rstar_max > p->hyp_S * (1.0 + 1e-12))
+            return fail(TEUK_ERR_ARG, "rho_max beyond scri (rho = S)");
+    } else if (p->coords != TEUK_COORDS_RSTAR) {
+        return fail(TEUK_ERR_ARG, "unknown coordinates");
+    }
     if (p->dt < 0.0 || !std::isfinite(p->dt)) return fail(TEUK_ERR_ARG, "dt must be >= 0");
     if (p->dt == 0.0 && !(p->cfl > 0.0 && p->cfl <= 1.0))
         return fail(TEUK_ERR_ARG, "cfl must be in (0, 1] when dt == 0");
@@ -235,10 +346,11 @@ teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
         for (int j = j0; j < j1; ++j) {
             double lam = 0.0;
             for (int i = 0; i < p->nr; ++i) {
-                PointCoef c = point_coefficients_rx(r[i], x[i], (j + 0.5) * dth, *p);
+                PointCoef c = node_coefficients(r[i], x[i], (j + 0.5) * dth, *p);
                 double kappa = c.Ath * (16.0 / 3.0) / (dth * dth) + std::fabs(c.Bth) * 1.5 / dth +
                                std::hypot(c.Cr, c.Ci);
-                lam = std::fmax(lam, c.b / h + std::sqrt(kappa));
+                const double speed = std::fmax(std::fabs(c.b), std::fabs(c.c));
+                lam = std::fmax(lam, speed / h + std::sqrt(kappa));
             }
             row_lam[j] = lam;
         }
@@ -253,7 +365,7 @@ teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
 
 size_t teuk_coeff_count(const teuk_params* p) {
     if (teuk_check_params(p) != TEUK_OK) return 0;
-    return (size_t)coef_planes(p->theta_mode) * (size_t)p->nr * (size_t)p->ntheta;
+    return (size_t)coef_planes(*p) * (size_t)p->nr * (size_t)p->ntheta;
 }
 
 teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coef) {
@@ -274,9 +386,10 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
     for (int j = j0; j < j1; ++j) {
         const double th = (j + 0.5) * dth;
         for (int i = 0; i < nr; ++i) {
-            PointCoef c = point_coefficients_rx(r[i], x[i], th, *p);
+            PointCoef c = node_coefficients(r[i], x[i], th, *p);
             const size_t q = (size_t)j * nr + i;
             coef[kCb * plane + q] = c6h * c.b;
+            if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) coef[kCc * plane + q] = c6h * c.c;
             coef[kCKr * plane + q] = c6h * c.Kr;
             coef[kCKi * plane + q] = c6h * c.Ki;
             coef[kCBr * plane + q] = dt * c.Btr;
@@ -289,6 +402,7 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
             const double A = dt * c.Ath / (12.0 * dth * dth);
             const double B = weno_th ? 0.0 : dt * c.Bth / (12.0 * dth);
             if (weno_th) coef[kCBth * plane + q] = dt * c.Bth / (6.0 * dth);
+            else if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) coef[kCBth * plane + q] = 0.0;
             double w[5] = {-A + B, 16.0 * A - 8.0 * B, -30.0 * A + dt * c.Cr,
                            16.0 * A + 8.0 * B, -A - B};
             // Rows outside [0, nth) mirror across the pole with parity sigma:

@@ -7,12 +7,13 @@
 
 namespace teuk {
 
-// Number of coefficient planes the stage kernel reads per grid node (one more
-// with the theta-WENO option: dt Bth / (6 dtheta)).
+// Number of coefficient planes per grid node: 11; 12 with the theta-WENO
+// option (dt Bth / (6 dtheta)); 13 on the hyperboloidal slices (the pi rows'
+// speed, plane 12; plane 11 is then unused and holds zeros).
 constexpr int kCoefPlanes = 11;
-constexpr int kCoefPlanesThetaWeno = 12;
-inline int coef_planes(int theta_mode) {
-    return theta_mode == TEUK_THETA_WENO5 ? kCoefPlanesThetaWeno : kCoefPlanes;
+inline int coef_planes(const teuk_params& p) {
+    if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) return 13;
+    return p.theta_mode == TEUK_THETA_WENO5 ? 12 : kCoefPlanes;
 }
 // Plane order (all pre-multiplied by dt):
 //   0 cb   = b/(6h)          1 cKr = Re K/(6h)     2 cKi = Im K/(6h)
@@ -22,7 +23,9 @@ inline int coef_planes(int theta_mode) {
 //          folded in).
 //   11     (theta-WENO option) dt Bth / (6 dtheta); the five stencil planes
 //          then hold only the second derivative and Re C.
-enum CoefPlane { kCb = 0, kCKr, kCKi, kCBr, kCBi, kCCi, kWm2, kWm1, kW0, kWp1, kWp2, kCBth };
+//   12     (hyperboloidal slices) cc = c/(6h), the pi rows' speed; in r* the
+//          pi rows use cb (c = b).
+enum CoefPlane { kCb = 0, kCKr, kCKi, kCBr, kCBi, kCCi, kWm2, kWm1, kW0, kWp1, kWp2, kCBth, kCc };
 
 // Forward-Euler step of one stage of p's integrator: dt for SSP-RK(3,3),
 // dt/6 for SSP-RK(10,4).
@@ -36,10 +39,13 @@ void clear_error();
 // r(r*) and the continuum coefficients at one node, real arithmetic.
 struct PointCoef {
     double b, Kr, Ki, Btr, Bti, Cr, Ci, Ath, Bth;
+    double c;   // the pi rows' speed (c = b in r*)
 };
 double r_of_rstar(double rstar, double M, double a, double* x_out);
 PointCoef point_coefficients(double rstar, double theta, const teuk_params& p);
 PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_params& p);
+PointCoef point_coefficients_hyp(double rho, double theta, const teuk_params& p);
+double horizon_rho(double M, double a, double S);
 
 double swsh(int s, int l, int m, double theta);
 uint64_t splitmix64(uint64_t& state);

@@ -371,7 +371,28 @@ __device__ __forceinline__ void fd6_ko8(const double* d, double& D6h, double& e8
     e8 = fma(35.0, d[3] - d[4], fma(21.0, d[5] - d[2], u));
 }
 
-template <int W, int STAGE, int THETA, class G, int SCHEME = 0>
+// Node k of a radial line f[0..nr) extended past either end (k in
+// [-3, nr+2]) by the quartic through the five edge nodes: the fifth
+// difference of the extended line vanishes, so each ghost follows from the
+// five values before it, u = 5 v0 - 10 v1 + 10 v2 - 5 v3 + v4 (v0 nearest).
+__device__ __noinline__ double ghost_value(const double* f, int nr, int k) {
+    if (k >= 0 && k < nr) return __ldg(f + k);
+    const bool left = k < 0;
+    const int step = left ? 1 : -1;
+    const int e = left ? 0 : nr - 1;
+    double v0 = __ldg(f + e), v1 = __ldg(f + e + step), v2 = __ldg(f + e + 2 * step);
+    double v3 = __ldg(f + e + 3 * step), v4 = __ldg(f + e + 4 * step);
+    const int n = left ? -k : k - (nr - 1);
+    for (int t = 0; t < n; ++t) {
+        const double u = fma(5.0, v0 - v3, fma(10.0, v2 - v1, v4));
+        v4 = v3; v3 = v2; v2 = v1; v1 = v0; v0 = u;
+    }
+    return v0;
+}
+
+// HYP: the hyperboloidal slices, whose pi rows have their own speed (plane
+// kCc); in r* they share the Psi rows' b.
+template <int W, int STAGE, int THETA, class G, int SCHEME = 0, bool HYP = false>
 __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw, int j,
                                             int i0, int p, double out[4]) {
     constexpr int NW = G::NW, FO = G::ND + G::NS;   // flux terms start at FO
@@ -395,7 +416,9 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     }
     const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
     const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
-    const double cb = __ldg(cf + kCb * P), cKr = __ldg(cf + kCKr * P);
+    const double cb = __ldg(cf + kCb * P);
+    const double cc = HYP ? __ldg(cf + kCc * P) : cb;
+    const double cKr = __ldg(cf + kCKr * P);
     const double cKi = __ldg(cf + kCKi * P), cBr = __ldg(cf + kCBr * P);
     const double cBi = __ldg(cf + kCBi * P), cCi = __ldg(cf + kCCi * P);
     double acc0, acc1, acc2, acc3;
@@ -407,14 +430,14 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     // Psi rows: dt (pi - b D_Psi)
     acc0 = fma(-cb, D0, acc0);
     acc1 = fma(-cb, D1, acc1);
-    // pi rows: dt (b D_pi + K D_Psi + Bt pi + i Im(C) Psi + theta terms)
-    acc2 = fma(cb, D2, acc2);
+    // pi rows: dt (c D_pi + K D_Psi + Bt pi + i Im(C) Psi + theta terms)
+    acc2 = fma(cc, D2, acc2);
     acc2 = fma(cKr, D0, acc2);
     acc2 = fma(-cKi, D1, acc2);
     acc2 = fma(cBr, pir, acc2);
     acc2 = fma(-cBi, pii, acc2);
     acc2 = fma(-cCi, psi, acc2);
-    acc3 = fma(cb, D3, acc3);
+    acc3 = fma(cc, D3, acc3);
     acc3 = fma(cKi, D0, acc3);
     acc3 = fma(cKr, D1, acc3);
     acc3 = fma(cBi, pir, acc3);
@@ -466,7 +489,7 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
 
 // One warp's work: segment seg_blk (nodes seg_blk*SEG ..) of theta row j of
 // the evolution described by A. sw is the warp's shared-memory block.
-template <int W, int STAGE, int THETA, int SEGV, int SCHEME = 0>
+template <int W, int STAGE, int THETA, int SEGV, int SCHEME = 0, bool HYP = false>
 __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, int lane, int j,
                                                 int seg_blk) {
     using G = std::conditional_t<SCHEME == 1, GeoFD<SEGV>, Geo<SEGV>>;
@@ -479,13 +502,19 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
 #define SD(c, k) sw[(c) * NW + ND + (k)]
 #define FL(c, k) sw[(c) * NW + ND + NS + (k)]
 
-    // 1. first differences d_k, k = i0-HALO .. (edge ghosts: d = 0)
+    // 1. first differences d_k, k = i0-HALO .. (ghosts: edge copies, d = 0;
+    //    on the hyperboloidal slices the quartic through the five edge nodes)
     for (int idx = lane; idx < 4 * ND; idx += 32) {
         const int c = idx / ND, k = idx - c * ND;
         const int g = i0 - HALO + k;
         const double* f = A.up + c * A.plane + row;
-        const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
-        DL(c, k) = __ldg(f + ib) - __ldg(f + ia);
+        if (HYP && (g < 0 || g >= nr - 1)) {
+            // nodes beyond nr+2 feed no stored node
+            DL(c, k) = g + 1 <= nr + 2 ? ghost_value(f, nr, g + 1) - ghost_value(f, nr, g) : 0.0;
+        } else {
+            const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
+            DL(c, k) = __ldg(f + ib) - __ldg(f + ia);
+        }
     }
     __syncwarp();
     if constexpr (SCHEME == 0) {
@@ -507,9 +536,9 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
     //    predicated)
     for (int p = lane; p < SEG; p += 64) {
         double ua[4], ub[4];
-        node_update<W, STAGE, THETA, G, SCHEME>(A, sw, j, i0, p, ua);
+        node_update<W, STAGE, THETA, G, SCHEME, HYP>(A, sw, j, i0, p, ua);
         const bool has_b = p + 32 < SEG;
-        if (has_b) node_update<W, STAGE, THETA, G, SCHEME>(A, sw, j, i0, p + 32, ub);
+        if (has_b) node_update<W, STAGE, THETA, G, SCHEME, HYP>(A, sw, j, i0, p + 32, ub);
         const long long P = A.plane;
         if (i0 + p < nr) {
             const long long q = row + i0 + p;
@@ -526,14 +555,14 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
 }
 
 // Single evolution: blockIdx.x = segment, blockIdx.y = block of WARPS rows.
-template <int W, int STAGE, int THETA>
+template <int W, int STAGE, int THETA, bool HYP = false>
 __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     constexpr int SEGV = Seg<W>::value;
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
-    process_segment<W, STAGE, THETA, SEGV>(A, sm[warp], lane, j, blockIdx.x);
+    process_segment<W, STAGE, THETA, SEGV, 0, HYP>(A, sm[warp], lane, j, blockIdx.x);
 }
 
 // FD6 + KO8 comparison scheme (Sec. 3.1.1), single evolution, centred theta.
@@ -616,22 +645,25 @@ static void eps_parts(double eps, int wprec, int* E, int* pow2, unsigned* mant_b
     *mant_bits = (127u << 23) + (unsigned)(kept << (24 - P));
 }
 
-template <int W, int THETA>
+template <int W, int THETA, bool HYP = false>
 static cudaError_t launch_stage_wt(const StageArgs& A, int stage, cudaStream_t st) {
     constexpr int SEG = Seg<W>::value;
     dim3 grid((A.nr + SEG - 1) / SEG, (A.nth + WARPS - 1) / WARPS);
     dim3 block(WARPS * 32);
     switch (stage) {
-    case 0: stage_kernel<W, 0, THETA><<<grid, block, 0, st>>>(A); break;
-    case 1: stage_kernel<W, 1, THETA><<<grid, block, 0, st>>>(A); break;
-    case 2: stage_kernel<W, 2, THETA><<<grid, block, 0, st>>>(A); break;
-    default: stage_kernel<W, 3, THETA><<<grid, block, 0, st>>>(A); break;
+    case 0: stage_kernel<W, 0, THETA, HYP><<<grid, block, 0, st>>>(A); break;
+    case 1: stage_kernel<W, 1, THETA, HYP><<<grid, block, 0, st>>>(A); break;
+    case 2: stage_kernel<W, 2, THETA, HYP><<<grid, block, 0, st>>>(A); break;
+    default: stage_kernel<W, 3, THETA, HYP><<<grid, block, 0, st>>>(A); break;
     }
     return cudaGetLastError();
 }
 
+// The hyperboloidal slices run with centred theta differences only.
 template <int W>
-static cudaError_t launch_stage_w(const StageArgs& A, int stage, int theta, cudaStream_t st) {
+static cudaError_t launch_stage_w(const StageArgs& A, int stage, int theta, bool hyp,
+                                  cudaStream_t st) {
+    if (hyp) return launch_stage_wt<W, TEUK_THETA_CENTERED4, true>(A, stage, st);
     return theta == TEUK_THETA_WENO5 ? launch_stage_wt<W, TEUK_THETA_WENO5>(A, stage, st)
                                      : launch_stage_wt<W, TEUK_THETA_CENTERED4>(A, stage, st);
 }
@@ -676,11 +708,12 @@ cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const doub
         return cudaGetLastError();
     }
     const int th = p.theta_mode;
+    const bool hyp = p.coords == TEUK_COORDS_HYPERBOLOIDAL;
     switch (p.wprec) {
-    case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, th, st);
-    case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, th, st);
-    case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, th, st);
-    default: return launch_stage_w<TEUK_W_BF16>(A, stage, th, st);
+    case TEUK_W_FP64: return launch_stage_w<TEUK_W_FP64>(A, stage, th, hyp, st);
+    case TEUK_W_FP32: return launch_stage_w<TEUK_W_FP32>(A, stage, th, hyp, st);
+    case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, th, hyp, st);
+    default: return launch_stage_w<TEUK_W_BF16>(A, stage, th, hyp, st);
     }
 }
 

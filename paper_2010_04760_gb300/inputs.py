@@ -5,12 +5,14 @@ arithmetic lives here. Both the CUDA path's tests/benchmarks and the oracle
 checks draw their inputs from it, so the two sides see identical data.
 
 Initial data (the paper's own run uses a Gaussian wave packet times a
-spherical harmonic, Sec. 4): Psi(r*, theta) = sum_l A_l exp(i phi_l)
-exp(-(r* - rc)^2 / (2 w^2)) sY_lm(theta), pi = 0. Amplitudes A_l ~ U(0.5, 1.5)
-and phases phi_l ~ U(0, 2 pi) come from ``numpy.random.default_rng(seed)``.
-The width w is the Gaussian's standard deviation.
+spherical harmonic, Sec. 4): Psi(x, theta) = sum_l A_l exp(i phi_l)
+exp(-(x - rc)^2 / (2 w^2)) sY_lm(theta), pi = 0, with x the radial coordinate
+(r*, or rho on the hyperboloidal slices, where Psi stands for the evolved
+Phi = r Delta^s Psi). Amplitudes A_l ~ U(0.5, 1.5) and phases
+phi_l ~ U(0, 2 pi) come from ``numpy.random.default_rng(seed)``. The width w
+is the Gaussian's standard deviation.
 
-Grid: r*_i = rs_min + i h, h = (rs_max - rs_min)/(nr - 1), i = 0..nr-1;
+Grid: x_i = rs_min + i h, h = (rs_max - rs_min)/(nr - 1), i = 0..nr-1;
 theta_j = (j + 1/2) pi / nth (cell centred).
 """
 from dataclasses import dataclass, field, replace
@@ -72,6 +74,9 @@ class Workload:
     t_end: float = 0.0
     nsteps: int = 0
     extra: dict = field(default_factory=dict)
+    coords: int = 0          # 0: BL t and r*; 1: hyperboloidal (tau, rho)
+    field: int = None        # evolved field (None: Psi in r*, Phi on the slices)
+    S: float = 20.0          # hyperboloidal slice parameter
 
     def with_(self, **kw):
         return replace(self, **kw)
@@ -171,6 +176,22 @@ TAIL_SCALAR = Workload(
     name="tail_s0_m0_16384x512", nr=16384, nth=512, rs_min=-5000.0, rs_max=5000.0,
     a=0.0, s=0, m=0, wprec="fp32", cfl=0.5, rc=50.0, width=4.0, ells=(0,), seed=3,
     t_end=1.0e4)
+
+
+def horizon_rho(M, a, S):
+    """rho of the outer horizon r_+ = M + sqrt(M^2 - a^2) on the slices."""
+    rp = M + sqrt(max(M * M - a * a, 0.0))
+    return rp * S / (rp + S)
+
+
+# The paper's own run (Sec. 4): extremal Kerr (a = M), s = -2, (l, m) = (2, 0),
+# a wave packet at rho = 1.0 of width 0.22 on the hyperboloidal slices with
+# S = 20, 16384 (rho) x 64 (theta) nodes from the horizon to scri.
+EXTREMAL_GRAV_HYP = Workload(
+    name="extremal_hyp_s-2_m0_16384x64", nr=16384, nth=64,
+    rs_min=horizon_rho(1.0, 1.0, 20.0), rs_max=20.0, a=1.0, s=-2, m=0,
+    wprec="fp32", cfl=0.5, rc=1.0, width=0.22, ells=(2,), seed=4, t_end=1000.0,
+    coords=1, S=20.0)
 
 
 def batch_workloads(n=64, seed=2026):

@@ -123,3 +123,81 @@ def test_build_coefficients_rejects_bad_dt():
     p = T.make_params(64, 16)
     with pytest.raises(T.TeukError):
         T.teuk_build_coefficients(p, 0.0)
+
+
+def _check_planes_against_oracle(p, co, dt, coords):
+    """The kernel planes of p against the oracle's coefficients co: radial
+    planes scaled by dt/(6h), the rest by dt (plane 12 = the pi rows' speed
+    on the hyperboloidal slices)."""
+    got = T.teuk_build_coefficients(p, dt)
+    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth, c = co
+    h = (p.rstar_max - p.rstar_min) / (p.nr - 1)
+    scale = np.max(np.abs(co), axis=(1, 2))
+    for k, (plane, ref) in enumerate([(0, dt * b / (6 * h)), (1, dt * Kr / (6 * h)),
+                                      (2, dt * Ki / (6 * h)), (3, dt * Br), (4, dt * Bi),
+                                      (5, dt * Ci)]):
+        np.testing.assert_allclose(got[plane], ref, rtol=1e-9, atol=1e-13 * dt * max(scale) / h)
+    if coords == 1:
+        np.testing.assert_allclose(got[12], dt * c / (6 * h), rtol=1e-9, atol=1e-14)
+        assert np.all(got[11] == 0.0)
+
+
+@pytest.mark.parametrize("a,s,m", [(0.0, 0, 0), (1.0, -2, 0), (0.7, -2, 2), (0.3, 1, -1),
+                                   (0.95, 2, 3)])
+def test_hyperboloidal_coefficients_agree_with_oracle(a, s, m):
+    """Sec. 2.2 slices: the host's closed forms (analytic d b/d rho) against
+    the oracle's (complex-step d b/d rho), horizon to scri."""
+    nr, nth, S, dt = 48, 10, 20.0, 0.01
+    p = T.make_params(nr, nth, a=a, s=s, m=m, coords=T.TEUK_COORDS_HYPERBOLOIDAL, hyp_S=S)
+    assert T.teuk_check_params(p) == T.TEUK_OK, T.teuk_last_error()
+    assert T.teuk_coeff_count(p) == 13 * nr * nth
+    g = o.grid(nr, nth, p.rstar_min, p.rstar_max, 1.0, a, s, m, coords=1, S=S)
+    _check_planes_against_oracle(p, o.coefficients(g), dt, 1)
+
+
+@pytest.mark.parametrize("a,s,m", [(0.0, 0, 0), (0.999, -2, 2), (0.4, -1, 1), (0.7, 2, 3)])
+def test_rescaled_field_coefficients_agree_with_oracle(a, s, m):
+    nr, nth, rs0, rs1, dt = 40, 12, -60.0, 120.0, 0.07
+    p = T.make_params(nr, nth, rs0, rs1, 1.0, a, s, m, field=T.TEUK_FIELD_PHI)
+    g = o.grid(nr, nth, rs0, rs1, 1.0, a, s, m, field=1)
+    _check_planes_against_oracle(p, o.coefficients(g), dt, 0)
+
+
+def test_hyperboloidal_argument_rules():
+    H = T.TEUK_COORDS_HYPERBOLOIDAL
+    ok = T.make_params(64, 16, a=0.6, s=-2, m=1, coords=H)
+    assert T.teuk_check_params(ok) == T.TEUK_OK
+    rhop = T.horizon_rho(1.0, 0.6, 20.0)
+    assert abs(ok.rstar_min - rhop) < 1e-15 and ok.rstar_max == 20.0
+    bad = [dict(field=T.TEUK_FIELD_PSI), dict(scheme=1), dict(theta_mode=1),
+           dict(hyp_S=0.5), dict(rstar_min=rhop * 0.999), dict(rstar_max=20.001),
+           dict(coords=2), dict(field=3)]
+    for kw in bad:
+        p = T.make_params(64, 16, a=0.6, s=-2, m=1, **{**dict(coords=H), **kw})
+        assert T.teuk_check_params(p) == T.TEUK_ERR_ARG, kw
+        assert T.teuk_last_error()
+    # a sub-range strictly inside [rho_+, S] is fine
+    assert T.teuk_check_params(T.make_params(64, 16, 2.0, 15.0, a=0.6, coords=H)) == T.TEUK_OK
+
+
+def test_hyperboloidal_time_step_uses_the_larger_speed():
+    """dt = cfl / max(max(|b|, |c|)/h + sqrt(kappa)) (the pi rows' speed c is
+    the larger one near the horizon, where b vanishes)."""
+    H = T.TEUK_COORDS_HYPERBOLOIDAL
+    p = T.make_params(256, 16, a=1.0, s=-2, m=0, coords=H, cfl=0.5)
+    dt = T.teuk_stable_dt(p)
+    g = o.grid(256, 16, p.rstar_min, p.rstar_max, 1.0, 1.0, -2, 0, coords=1, S=20.0)
+    b, Kr, Ki, Br, Bi, Cr, Ci, Ath, Bth, c = o.coefficients(g)
+    h = (p.rstar_max - p.rstar_min) / 255
+    dth = np.pi / 16
+    kap = Ath * (16 / 3) / dth ** 2 + np.abs(Bth) * 1.5 / dth + np.hypot(Cr, Ci)
+    lam = np.max(np.maximum(np.abs(b), np.abs(c)) / h + np.sqrt(kap))
+    assert abs(dt - 0.5 / lam) < 1e-9 * dt
+
+
+def test_batches_reject_hyperboloidal_members():
+    """Argument checks run before any device call, so this needs no GPU."""
+    ps = [T.make_params(64, 16), T.make_params(64, 16, coords=T.TEUK_COORDS_HYPERBOLOIDAL)]
+    with pytest.raises(T.TeukError):
+        T.teuk_batch_create(ps, stream=0, autotune=False)
+    assert "r* coordinates" in T.teuk_last_error()
