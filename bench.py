@@ -248,6 +248,28 @@ def time_batch(T, torch, stream, steps=32):
             "ctas_per_sm": ctas, "wprec": "fp32"}
 
 
+def time_paper_run(T, torch, stream, steps=200):
+    """Throughput on the paper's own run (Sec. 4): 16384 (rho) x 64 (theta)
+    on the hyperboloidal slices, extremal Kerr, s = -2, (l, m) = (2, 0),
+    binary32 weights; state and 13 coefficient planes ~143 MB, above L2."""
+    wl = I.EXTREMAL_GRAV_HYP
+    h = T.teuk_create(T.params_from_workload(wl), stream)
+    T.teuk_set_state(h, I.initial_data(wl), 0.0)
+    T.teuk_step(h, 32)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    T.teuk_step(h, steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = T.teuk_check_finite(h)
+    h.close()
+    return {"value": wl.nr * wl.nth * 3 * steps / (ms * 1e-3), "unit": UNIT,
+            "workload": wl.name, "steps": steps, "ms_per_step": ms / steps, "wprec": wl.wprec,
+            "finite": st == T.TEUK_OK}
+
+
 def oracle_rate(nsteps_budget_s=12.0, wprec="fp32", max_steps=400):
     """Oracle point-stage updates/s on the workload, over a bounded number of
     RK steps chosen to take about nsteps_budget_s seconds."""
@@ -333,6 +355,7 @@ def main():
     e2e_s = max_over_ranks(e2e_s, world, device)
     err, t_err = waveform_error(T, torch, stream) if rank == 0 else (None, None)
     batch = time_batch(T, torch, stream) if rank == 0 else None
+    paper_run = time_paper_run(T, torch, stream) if rank == 0 else None
 
     fp64_peak_tf = 2.0 * T.teuk_fp64_fma_rate(stream) / 1e12      # measured live
     value = weak_scaling_value(POINTS * 3, args.steps, world, ms32)
@@ -373,6 +396,7 @@ def main():
         "e2e": {"value": POINTS * 3 * e2e_steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "batched_64_uneven_evolutions": batch,
+        "paper_run_hyperboloidal_16384x64": paper_run,
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
     }
