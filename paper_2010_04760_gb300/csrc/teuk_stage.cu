@@ -554,11 +554,22 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
 #undef FL
 }
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later): the
+// block first waits until the previous kernel of the stream has completed and
+// its writes are visible (a no-op when the launch did not ask for early
+// scheduling), then lets the next kernel's blocks be scheduled onto SMs this
+// grid no longer fills; they in turn wait here for this grid to complete.
+__device__ __forceinline__ void dependent_launch_gate() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Single evolution: blockIdx.x = segment, blockIdx.y = block of WARPS rows.
 template <int W, int STAGE, int THETA, bool HYP = false>
 __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     constexpr int SEGV = Seg<W>::value;
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
+    dependent_launch_gate();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
@@ -645,18 +656,51 @@ static void eps_parts(double eps, int wprec, int* E, int* pow2, unsigned* mant_b
     *mant_bits = (127u << 23) + (unsigned)(kept << (24 - P));
 }
 
+// Launch with programmatic stream serialisation when the grid fills at least
+// one wave of resident blocks: the kernel may then be scheduled onto the SMs
+// its predecessor's last wave leaves free, before that predecessor completes;
+// its dependent_launch_gate keeps every memory access after the completion.
+// A grid smaller than one wave is launched plainly: every block of such a
+// predecessor starts at once and releases its dependents immediately, so they
+// would crowd onto the few free slots unevenly (measured: 8% slower on the
+// binary64-weight kernel at 2048 x 128, against 3% faster at 1.7 waves).
+static cudaError_t launch_early(void (*kernel)(StageArgs), dim3 grid, dim3 block,
+                                const StageArgs& A, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel,
+                                                          (int)(block.x * block.y * block.z), 0);
+    if (e != cudaSuccess) return e;
+    if ((long long)grid.x * grid.y * grid.z < (long long)sms * per_sm) {
+        kernel<<<grid, block, 0, st>>>(A);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, A);
+}
+
 template <int W, int THETA, bool HYP = false>
 static cudaError_t launch_stage_wt(const StageArgs& A, int stage, cudaStream_t st) {
     constexpr int SEG = Seg<W>::value;
     dim3 grid((A.nr + SEG - 1) / SEG, (A.nth + WARPS - 1) / WARPS);
     dim3 block(WARPS * 32);
     switch (stage) {
-    case 0: stage_kernel<W, 0, THETA, HYP><<<grid, block, 0, st>>>(A); break;
-    case 1: stage_kernel<W, 1, THETA, HYP><<<grid, block, 0, st>>>(A); break;
-    case 2: stage_kernel<W, 2, THETA, HYP><<<grid, block, 0, st>>>(A); break;
-    default: stage_kernel<W, 3, THETA, HYP><<<grid, block, 0, st>>>(A); break;
+    case 0: return launch_early(stage_kernel<W, 0, THETA, HYP>, grid, block, A, st);
+    case 1: return launch_early(stage_kernel<W, 1, THETA, HYP>, grid, block, A, st);
+    case 2: return launch_early(stage_kernel<W, 2, THETA, HYP>, grid, block, A, st);
+    default: return launch_early(stage_kernel<W, 3, THETA, HYP>, grid, block, A, st);
     }
-    return cudaGetLastError();
 }
 
 // The hyperboloidal slices run with centred theta differences only.
