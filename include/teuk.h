@@ -282,6 +282,20 @@ teuk_status teuk_set_gaussian(teuk_handle* h, double rc, double width, const dou
 teuk_status teuk_set_state(teuk_handle* h, const double* u_host, double t);
 teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out);
 
+/* Asynchronous forms: the copy is only enqueued on the handle's stream, in
+ * order with teuk_step, and the call returns at once. The host buffer
+ * (4*ntheta*nr doubles) must stay valid and, for set, unchanged until the
+ * stream has passed the copy; for get, its contents are defined only after
+ * teuk_synchronize. Use page-locked (pinned) host memory: with pageable
+ * memory the copy may complete before the call returns. teuk_set_state_async
+ * sets the handle's time to t at once. Several handles, each on its own
+ * stream, overlap one evolution's copies with another's stepping. */
+teuk_status teuk_set_state_async(teuk_handle* h, const double* u_host, double t);
+teuk_status teuk_get_state_async(teuk_handle* h, double* u_host);
+
+/* Wait until everything enqueued on the handle's stream has completed. */
+teuk_status teuk_synchronize(teuk_handle* h);
+
 /* Advance nsteps steps of p's integrator (3 fused stage launches each for
  * SSP-RK(3,3), 11 for SSP-RK(10,4)), replayed from a captured CUDA graph.
  * Asynchronous on the handle's stream. */

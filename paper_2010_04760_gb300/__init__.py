@@ -79,6 +79,9 @@ def lib():
             "teuk_set_state": (I, [P, P, D]),
             "teuk_set_gaussian": (I, [P, D, D, P, I, ctypes.c_uint64]),
             "teuk_get_state": (I, [P, P, P]),
+            "teuk_set_state_async": (I, [P, P, D]),
+            "teuk_get_state_async": (I, [P, P]),
+            "teuk_synchronize": (I, [P]),
             "teuk_step": (I, [P, I64]),
             "teuk_observe": (I, [P, D, P, P, P]),
             "teuk_check_finite": (I, [P]),
@@ -299,6 +302,29 @@ def teuk_get_state(h, out=None):
     t = ctypes.c_double()
     _check(lib().teuk_get_state(h.ptr, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
     return out, t.value
+
+
+def teuk_set_state_async(h, u, t=0.0):
+    """Enqueue the host-to-device copy of u (keep u alive and unchanged, and
+    preferably page-locked, until the stream has passed the copy)."""
+    arr = np.ascontiguousarray(u, dtype=np.float64)
+    if arr is not u:
+        raise ValueError("teuk_set_state_async needs a C-contiguous float64 array "
+                         "(a temporary copy would be freed before the copy runs)")
+    _check(lib().teuk_set_state_async(h.ptr, arr.ctypes.data_as(ctypes.c_void_p), float(t)))
+
+
+def teuk_get_state_async(h, out):
+    """Enqueue the device-to-host copy of the state into out (defined after
+    teuk_synchronize)."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.size == 4 * h.p.ntheta * h.p.nr):
+        raise ValueError("out must be a C-contiguous float64 array of 4*ntheta*nr values")
+    _check(lib().teuk_get_state_async(h.ptr, out.ctypes.data_as(ctypes.c_void_p)))
+
+
+def teuk_synchronize(h):
+    _check(lib().teuk_synchronize(h.ptr))
 
 
 def teuk_step(h, nsteps):

@@ -543,6 +543,30 @@ teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out) {
     return TEUK_OK;
 }
 
+teuk_status teuk_set_state_async(teuk_handle* h, const double* u_host, double t) {
+    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+    TEUK_CUDA(cudaMemcpyAsync(h->u, u_host, 4 * h->plane() * sizeof(double),
+                              cudaMemcpyHostToDevice, h->stream));
+    h->t = t;
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_get_state_async(teuk_handle* h, double* u_host) {
+    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+    TEUK_CUDA(cudaMemcpyAsync(u_host, h->u, 4 * h->plane() * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+    clear_error();
+    return TEUK_OK;
+}
+
+teuk_status teuk_synchronize(teuk_handle* h) {
+    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+    TEUK_CUDA(cudaStreamSynchronize(h->stream));
+    clear_error();
+    return TEUK_OK;
+}
+
 teuk_status teuk_set_initial(teuk_handle* h, const double* psi, const double* pi) {
     if (!h || !psi || !pi) return fail(TEUK_ERR_ARG, "NULL argument");
     const size_t n = h->plane();
