@@ -47,8 +47,8 @@ BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel source it
 # was taken on, identified by its sha256.
 NCU_TRAFFIC = {"source": "paper_2010_04760_gb300/csrc/teuk_stage.cu",
-               "sha256": "ab98ffe205311fce520a3f1057876da4759aa6ea6e572bf7fcf14fb7f59367d3",
-               "bytes_per_launch": (31477504 + 39867136 + 39867136) / 3.0}
+               "sha256": "60dc3b3fbe0c071b5d062117192b12a54bd0d48f69ce842b6a7f7664eae721a9",
+               "bytes_per_launch": (31478272 + 39867392 + 39867904) / 3.0}
 
 
 def ncu_traffic():
