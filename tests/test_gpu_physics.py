@@ -6,6 +6,9 @@ about 5x the value measured on GB300):
   every 100 steps to t = 150 M: binary32 1e-9, binary16 1e-5, bfloat16 1e-4.
   Extremal scalar, 8192 x 256, to t = 100 M, the horizon gather (Psi, pi,
   dPsi/dr* at the innermost node): binary32 1e-9, binary16 1e-5, bfloat16 1e-4.
+  The same physics on the hyperboloidal slices, 4096 x 64 to tau = 100 M, where
+  node 0 is the horizon and the gather holds Phi, pi and the Aretakis charge
+  dPhi/drho: binary32 1e-11, binary16 5e-7, bfloat16 2e-6.
 Price tail: the local index p = t dPsi/dt / Psi at r* = 20 M of an l = 0
 scalar pulse (a = 0) tends to -3 (Sec. 3, Sec. 4); the GPU reproduces the
 oracle's p(t). On the hyperboloidal slices (Sec. 2.2) the same data decays as
@@ -188,3 +191,31 @@ def test_aretakis_horizon_laws_of_the_paper_run():
         i50, i300 = np.argmin(np.abs(ts - 50.0)), np.argmin(np.abs(ts - 300.0))
         drifts.append(abs(dphi[i300] / dphi[i50] - 1.0))
     assert drifts[1] < 0.75 * drifts[0], drifts
+
+
+def test_aretakis_charge_drift_of_reduced_weights_on_the_slices():
+    """Extremal scalar, l = 0 + 2 packet on the horizon (the physics of the
+    8192 x 256 extremal workload) on the hyperboloidal slices: the horizon
+    gather every 5 M to tau = 100 M with reduced weights against binary64
+    weights."""
+    wl = I.EXTREMAL_GRAV_HYP.with_(nr=4096, nth=64, s=0, m=0, ells=(0, 2), rc=1.0, width=0.22,
+                                   seed=2)
+
+    def gather(wprec):
+        h = T.teuk_create(T.params_from_workload(wl, wprec=wprec))
+        T.teuk_set_state(h, I.initial_data(wl), 0.0)
+        _, dt, _ = T.teuk_get_info(h)
+        n = int(round(5.0 / dt))
+        out, t = [], 0.0
+        while t < 100.0:
+            T.teuk_step(h, n)
+            _, hz, t = T.teuk_observe(h, wl.S)
+            out.append(hz.copy())
+        h.close()
+        return np.array(out)
+
+    ref = gather("fp64")
+    for wprec, bound in (("fp32", 1e-11), ("fp16", 5e-7), ("bf16", 2e-6)):
+        hz = gather(wprec)
+        assert _rel(hz, ref) <= bound, (wprec, _rel(hz, ref))
+        assert _rel(hz[:, :, 4:], ref[:, :, 4:]) <= bound, (wprec, "charge")
