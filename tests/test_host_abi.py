@@ -2,6 +2,7 @@
 symbol include/teuk.h declares, arguments are validated, and the host
 coefficient generator (independent code) agrees with the oracle."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -201,3 +202,25 @@ def test_batches_reject_hyperboloidal_members():
     with pytest.raises(T.TeukError):
         T.teuk_batch_create(ps, stream=0, autotune=False)
     assert "r* coordinates" in T.teuk_last_error()
+
+
+def test_params_struct_layout_matches_the_header(tmp_path):
+    """The binding's teuk_params has the header's field order, offsets and
+    size (a C program compiled against include/teuk.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [f[0] for f in T.teuk_params._fields_]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("{n} %zu\\n", offsetof(teuk_params, {n}));\n' for n in names)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "teuk.h"\nint main(void) {\n'
+                   + body + '    printf("sizeof %zu\\n", sizeof(teuk_params));\n    return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for n in names:
+        assert int(got[n]) == getattr(T.teuk_params, n).offset, n
+    assert int(got["sizeof"]) == ctypes.sizeof(T.teuk_params)
