@@ -90,7 +90,8 @@ __global__ void nonfinite_kernel(const double* __restrict__ u, long long n, int*
     if (bad && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
-// obs[2j..] = Psi at (ie, j); obs[2 nth + 6j ..] = Psi, pi, dPsi/dr* at i = 0.
+// obs[2j..] = Psi at (ie, j); obs[2 nth + 6j ..] = Psi, pi, dPsi/dx at i = 0
+// (x = r* or rho).
 __global__ void observe_kernel(const double* __restrict__ u, int nr, int nth, long long plane,
                                int ie, double inv2h, double* obs) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,10 +1,13 @@
-// Fused WENO5 / Teukolsky right-hand side / SSP-RK(3,3) stage kernel for
-// sm_103a, and the stateless device entry points of the C ABI.
+// Fused WENO5 / Teukolsky right-hand side / Runge-Kutta stage kernel for
+// sm_103a (SSP-RK(3,3) stages, or the forward-Euler stages of SSP-RK(10,4)),
+// and its launch code.
 //
-// One warp owns a segment of SEG consecutive r* nodes of one theta row. It
+// One warp owns a segment of SEG consecutive radial nodes (r*, or rho on the
+// hyperboloidal slices) of one theta row. It
 //   1. forms the binary64 first differences d_k = f_{k+1} - f_k of the four
-//      components over the segment plus its halo (r* ghosts copy the edge
-//      value, Sec. 3.1 reading),
+//      components over the segment plus its halo (ghosts copy the edge value
+//      in r*; on the hyperboloidal slices they extrapolate the quartic
+//      through the five edge nodes),
 //   2. forms s_k = d_{k-1} - 2 d_k + d_{k+1},
 //   3. at every interface computes the nonlinear weights (Sec. 3.1.2) in the
 //      requested precision (Sec. 3.1.3) and the binary64 flux term
@@ -13,8 +16,9 @@
 //      with x = (d_{i-2}, d_{i-1}, d_i, d_{i+1}); the negative-direction flux
 //      is its mirror image (x = d_{i+2}, d_{i+1}, d_i, d_{i-1}, G = -F),
 //   4. at every node forms 6 h D = 6 d + F_{i+1/2} - F_{i-1/2}, the theta
-//      stencil, the right-hand side -(M du + L u + A u) (Sec. 2.3) and the
-//      SSP-RK(3,3) combination (Sec. 3.2), and stores the new stage.
+//      stencil, the right-hand side -(M du + L u + A u) (Sec. 2.3; the pi
+//      rows move with their own speed c on the hyperboloidal slices) and the
+//      Runge-Kutta combination (Sec. 3.2), and stores the new stage.
 // Every binary64 quantity is formed once per node (no recomputation inside a
 // segment); the weights run on the FP32 pipes. The only binary64 operations
 // are the differences, the weighted flux combination, the right-hand side and
@@ -41,7 +45,7 @@ namespace teuk {
 constexpr int WARPS = TEUK_WARPS;  // theta rows per CTA (one per warp)
 #define TEUK_BOUNDS __launch_bounds__(TEUK_WARPS * 32, TEUK_MINB)
 
-// r* nodes per warp: 32 with reduced-precision weights, 64 with binary64
+// Radial nodes per warp: 32 with reduced-precision weights, 64 with binary64
 // weights (each the measured best on GB300 for the 2048 x 128 workload).
 template <int W> struct Seg {
 #ifdef TEUK_SEG
@@ -63,7 +67,7 @@ template <int S> struct GeoFD {
 };
 
 struct StageArgs {
-    const double* coef;   // kCoefPlanes planes of nth*nr
+    const double* coef;   // coef_planes(p) planes of nth*nr
     const double* un;     // u^n (stages 2, 3)
     const double* up;     // u^{(s-1)}, the operator's argument
     double* out;          // may alias un (read only at the same node)
