@@ -400,6 +400,10 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "fp64_weights": {"value": value64, "ms_per_step": ms64 / args.steps},
         "mixed_speedup_vs_fp64_weights": value / value64,
+        "paper_mixed_speedup_context": {
+            "value": 3.3, "what": "binary128 state with binary64 weights vs all-binary128, "
+            "WENO5 in rho, 16384 x 64 (Sec. 4-5)", "hardware": "not stated in the paper "
+            "(its GPU runs use V100 nodes)", "comparable": False},
         "waveform_rel_l2_fp32_vs_fp64_weights": err,
         "waveform_error_window": f"Psi(r*=50M, all theta) every 100 steps to t={t_err:.1f}M",
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_derived,

@@ -254,3 +254,33 @@ def test_price_tails_at_horizon_and_scri_on_the_hyperboloidal_grid():
     late = ts[1:-1] > 300.0
     assert np.all(np.abs(index(hor)[late] + 3.0) < 0.1), index(hor)[late]
     assert np.all(np.abs(index(scri)[late] + 2.0) < 0.15), index(scri)[late]
+
+
+def test_aretakis_laws_on_the_extremal_horizon():
+    """The paper's own run (Sec. 4: extremal Kerr, s = -2, (l, m) = (2, 0),
+    packet on the horizon) in the oracle: Phi on the horizon decays as
+    tau^-1 (Aretakis), and the radial derivative on the horizon (the charge,
+    conserved in the continuum) drifts less when the grid is refined."""
+    from paper_2010_04760_gb300 import inputs as I
+    drift = []
+    for nr in (1024, 2048):
+        wl = I.EXTREMAL_GRAV_HYP.with_(nr=nr, nth=12)
+        g = o.grid(nr, 12, wl.rs_min, wl.rs_max, 1.0, 1.0, -2, 0, coords=1, S=20.0)
+        co = o.coefficients(g)
+        h = (wl.rs_max - wl.rs_min) / (nr - 1)
+        dth = np.pi / 12
+        kap = co[7] * 16 / 3 / dth ** 2 + np.abs(co[8]) * 1.5 / dth + np.hypot(co[5], co[6])
+        dt = 0.5 / np.max(np.maximum(np.abs(co[0]), np.abs(co[9])) / h + np.sqrt(kap))
+        u = I.initial_data(wl)
+        t, seen = 0.0, []
+        for tk in (20.0, 40.0, 60.0):
+            n = int(round((tk - t) / dt))
+            u = o.rk3_step(g, co, dt, u, n)
+            t += n * dt
+            _, hz = o.observe(g, u, 20.0)
+            seen.append((t, hz[6, 0], hz[6, 4]))
+        (t1, p1, _), (t2, p2, _), (t3, p3, _) = seen
+        assert abs(np.log(p3 / p2) / np.log(t3 / t2) + 1.0) < 0.1, (nr, seen)
+        assert abs(np.log(p2 / p1) / np.log(t2 / t1) + 1.0) < 0.15, (nr, seen)
+        drift.append(abs(seen[2][2] / seen[0][2] - 1.0))
+    assert drift[1] < 0.75 * drift[0], drift
