@@ -47,8 +47,8 @@ BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel source it
 # was taken on, identified by its sha256.
 NCU_TRAFFIC = {"source": "paper_2010_04760_gb300/csrc/teuk_stage.cu",
-               "sha256": "60dc3b3fbe0c071b5d062117192b12a54bd0d48f69ce842b6a7f7664eae721a9",
-               "bytes_per_launch": (31478272 + 39867392 + 39867904) / 3.0}
+               "sha256": "4a40a9b9e561d6189f281c8316a51bf1e230e9c8de4787cec20e9a2fe1f71103",
+               "bytes_per_launch": (31478784 + 39867648 + 39867904) / 3.0}
 
 
 def ncu_traffic():
