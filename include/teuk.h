@@ -77,7 +77,8 @@ typedef enum {
                                  sixth-order centred differences with the
                                  Kreiss-Oliger term sigma h^7 D+^4 D-^4 / 256
                                  subtracted from every component (the damping
-                                 sign); centred theta only, no weights       */
+                                 sign); centred theta only, no weights; the
+                                 ghosts are those of the coordinates         */
 } teuk_scheme;
 
 /* Time integrator (Sec. 3.2). */
@@ -101,9 +102,9 @@ typedef enum {
                                       ghosts extrapolate the quartic through
                                       the five edge nodes. The pi rows move
                                       with their own speed -c (M33 = -c,
-                                      c = Atr + b). Requires TEUK_FIELD_PHI,
-                                      TEUK_SCHEME_WENO5 and
-                                      TEUK_THETA_CENTERED4; not in batches.   */
+                                      c = Atr + b). Requires TEUK_FIELD_PHI
+                                      and TEUK_THETA_CENTERED4; not in
+                                      batches. Both radial schemes.           */
 } teuk_coords;
 
 /* Evolved field. */

@@ -152,10 +152,13 @@ def weno5_weights(f5, dir, wprec="fp64", eps=1e-6):
     return out
 
 
-def fd6_ko8_1d(f, h, sigma=0.01, periodic=True):
+def fd6_ko8_1d(f, h, sigma=0.01, periodic=True, bc=None):
+    """bc: 0 edge copy, 1 periodic, 2 polynomial extrapolation (default from
+    ``periodic``)."""
     f = _f64(f)
     D, Q = np.zeros(f.size), np.zeros(f.size)
-    _load().orc_fd6_ko8_1d(_ptr(f), f.size, h, sigma, int(periodic), _ptr(D), _ptr(Q))
+    bc = int(periodic) if bc is None else int(bc)
+    _load().orc_fd6_ko8_1d(_ptr(f), f.size, h, sigma, bc, _ptr(D), _ptr(Q))
     return D, Q
 
 

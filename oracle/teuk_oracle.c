@@ -36,10 +36,11 @@
  *    rounded; alpha normalised by the smallest (eps + IS). omega_0, omega_2
  *    promoted to binary64 and omega_1 = 1 - omega_0 - omega_2 there (Sec. 3.1.3).
  *  - WENO epsilon: a parameter (1e-6 by default), unstated in the paper.
- *  - Comparison scheme (scheme 1, Sec. 3.1.1): the sixth-order centred r*
+ *  - Comparison scheme (scheme 1, Sec. 3.1.1): the sixth-order centred radial
  *    derivative for all four components and the Kreiss-Oliger term
  *    sigma h^7 D+^4 D-^4 / 256 subtracted from every component's right-hand
- *    side (the sign that damps), with edge-copy ghosts as for WENO.
+ *    side (the sign that damps), with the same ghosts as for WENO (edge
+ *    copies in r*, the quartic extrapolation on the hyperboloidal grid).
  */
 #include <math.h>
 #include <complex.h>
@@ -477,17 +478,20 @@ void orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
 /*         / (60 h)                                                          */
 /* and the Kreiss-Oliger operator Q = sigma h^7 D+^4 D-^4 / 256 with          */
 /* D+ u_j = (u_{j+1} - u_j)/h, D- u_j = (u_j - u_{j-1})/h, applied here       */
-/* literally (nested differences). Ghosts: periodic wrap or edge copies.      */
+/* literally (nested differences). Ghosts (bc): 0 edge copies, 1 periodic    */
+/* wrap, 2 polynomial extrapolation (extrap_ghost).                          */
 /* ------------------------------------------------------------------------ */
-void orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int periodic,
+void orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int bc,
                     double* D, double* Q) {
     const int G = 4;                                  /* ghost width */
     int m = n + 2 * G;
     double* a = (double*)malloc(sizeof(double) * m);
     double* b = (double*)malloc(sizeof(double) * m);
     for (int k = -G; k < n + G; ++k) {
-        int src = periodic ? ((k % n) + n) % n : (k < 0 ? 0 : (k >= n ? n - 1 : k));
-        a[k + G] = f[src];
+        if (k >= 0 && k < n) a[k + G] = f[k];
+        else if (bc == 1) a[k + G] = f[((k % n) + n) % n];
+        else if (bc == 2) a[k + G] = extrap_ghost(f, n, k, EXTRAP_DEG);
+        else a[k + G] = f[k < 0 ? 0 : n - 1];
     }
     for (int j = 0; j < n; ++j) {
         const double* u = &a[j + G];
@@ -529,8 +533,8 @@ void orc_rhs(const orc_grid* g, const double* coef, const double* u, double* F) 
         double* Qc = (double*)calloc(4 * (size_t)nr, sizeof(double));
         for (int c = 0; c < 4; ++c) {
             if (g->scheme == 1) {
-                orc_fd6_ko8_1d(&u[c * plane + (long)j * nr], nr, h, g->ko_sigma, 0,
-                               &Dc[c * nr], &Qc[c * nr]);
+                orc_fd6_ko8_1d(&u[c * plane + (long)j * nr], nr, h, g->ko_sigma,
+                               g->coords == 1 ? 2 : 0, &Dc[c * nr], &Qc[c * nr]);
             } else {
                 int dir = (c < 2) ? +1 : -1;
                 orc_weno5_deriv_1d(&u[c * plane + (long)j * nr], nr, h, dir, g->wprec,

@@ -56,7 +56,7 @@ void   orc_weno5_weights(int wprec, int dir, const double* f5, double eps,
                          double w[3]);
 double orc_weno5_flux(int wprec, int dir, const double* f5, double eps,
                       const double* force_w, double w_out[3], double q_out[3]);
-void   orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int periodic,
+void   orc_fd6_ko8_1d(const double* f, int n, double h, double sigma, int bc,
                       double* D, double* Q);
 void   orc_weno5_deriv_1d(const double* f, int n, double h, int dir, int wprec,
                           double eps, int bc, const double* force_w,

@@ -376,7 +376,7 @@ __device__ __forceinline__ void fd6_ko8(const double* d, double& D6h, double& e8
 }
 
 // Node k of a radial line f[0..nr) extended past either end (k in
-// [-3, nr+2]) by the quartic through the five edge nodes: the fifth
+// [-4, nr+3]) by the quartic through the five edge nodes: the fifth
 // difference of the extended line vanishes, so each ghost follows from the
 // five values before it, u = 5 v0 - 10 v1 + 10 v2 - 5 v3 + v4 (v0 nearest).
 __device__ __noinline__ double ghost_value(const double* f, int nr, int k) {
@@ -513,8 +513,9 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
         const int g = i0 - HALO + k;
         const double* f = A.up + c * A.plane + row;
         if (HYP && (g < 0 || g >= nr - 1)) {
-            // nodes beyond nr+2 feed no stored node
-            DL(c, k) = g + 1 <= nr + 2 ? ghost_value(f, nr, g + 1) - ghost_value(f, nr, g) : 0.0;
+            // nodes beyond nr-1+HALO feed no stored node
+            DL(c, k) = g + 1 <= nr - 1 + HALO ? ghost_value(f, nr, g + 1) - ghost_value(f, nr, g)
+                                              : 0.0;
         } else {
             const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
             DL(c, k) = __ldg(f + ib) - __ldg(f + ia);
@@ -580,16 +581,17 @@ __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     process_segment<W, STAGE, THETA, SEGV, 0, HYP>(A, sm[warp], lane, j, blockIdx.x);
 }
 
-// FD6 + KO8 comparison scheme (Sec. 3.1.1), single evolution, centred theta.
-template <int STAGE>
+// FD6 + KO8 comparison scheme (Sec. 3.1.1), single evolution, centred theta;
+// HYP as for stage_kernel.
+template <int STAGE, bool HYP = false>
 __global__ void TEUK_BOUNDS fd6_stage_kernel(const StageArgs A) {
     constexpr int SEGV = 32;
     __shared__ double sm[WARPS][4 * GeoFD<SEGV>::NW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
-    process_segment<TEUK_W_FP64, STAGE, TEUK_THETA_CENTERED4, SEGV, 1>(A, sm[warp], lane, j,
-                                                                      blockIdx.x);
+    process_segment<TEUK_W_FP64, STAGE, TEUK_THETA_CENTERED4, SEGV, 1, HYP>(A, sm[warp], lane, j,
+                                                                           blockIdx.x);
 }
 
 // Batched evolutions: one work item is a block of WARPS rows x one segment of
@@ -748,10 +750,18 @@ cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const doub
     if (p.scheme == TEUK_SCHEME_FD6_KO8) {
         A.ko = h * p.ko_sigma / (256.0 * ((p.rstar_max - p.rstar_min) / (p.nr - 1)));
         dim3 grid((A.nr + 31) / 32, (A.nth + WARPS - 1) / WARPS), block(WARPS * 32);
-        switch (stage) {
-        case 0: fd6_stage_kernel<0><<<grid, block, 0, st>>>(A); break;
-        case 1: fd6_stage_kernel<1><<<grid, block, 0, st>>>(A); break;
-        default: fd6_stage_kernel<2><<<grid, block, 0, st>>>(A); break;
+        if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) {
+            switch (stage) {
+            case 0: fd6_stage_kernel<0, true><<<grid, block, 0, st>>>(A); break;
+            case 1: fd6_stage_kernel<1, true><<<grid, block, 0, st>>>(A); break;
+            default: fd6_stage_kernel<2, true><<<grid, block, 0, st>>>(A); break;
+            }
+        } else {
+            switch (stage) {
+            case 0: fd6_stage_kernel<0><<<grid, block, 0, st>>>(A); break;
+            case 1: fd6_stage_kernel<1><<<grid, block, 0, st>>>(A); break;
+            default: fd6_stage_kernel<2><<<grid, block, 0, st>>>(A); break;
+            }
         }
         return cudaGetLastError();
     }

@@ -89,6 +89,29 @@ def test_hyperboloidal_operator_parity(wprec, shape, phys):
                 terms=term_scale(u, 1.0, g, co))
 
 
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("phys", PHYS)
+def test_hyperboloidal_fd6_ko8_operator_parity(shape, phys):
+    """The comparison scheme (Sec. 3.1.1) on the slices, where the paper makes
+    its WENO-versus-dissipation comparison: FD6 derivative, KO8 term and the
+    pi rows' own speed, with four extrapolated ghosts per end."""
+    nr, nth = shape
+    a, s, m = phys
+    lo = I.horizon_rho(1.0, a, S)
+    for smooth in (True, False):
+        u = I.random_state(nr, nth, nr * 11 + nth, smooth=smooth)
+        g = o.grid(nr, nth, lo, S, 1.0, a, s, m, scheme=1, ko_sigma=0.2, coords=1, S=S)
+        co = o.coefficients(g)
+        p = T.make_params(nr, nth, lo, S, 1.0, a, s, m, scheme=1, ko_sigma=0.2, coords=H,
+                          hyp_S=S)
+        coef = dev(T.teuk_build_coefficients(p, 1.0))
+        ud = dev(u)
+        out = torch.empty_like(ud)
+        T.teuk_stage_dev(p, 1.0, coef, None, ud, out, 0)
+        compare(host(out), o.rhs(g, co, u), what=f"hyp fd6 {shape} {phys} smooth={smooth}",
+                terms=term_scale(u, 1.0, g, co))
+
+
 @pytest.mark.parametrize("wprec", ["fp64", "fp32"])
 def test_hyperboloidal_sub_range_parity(wprec):
     """A range strictly inside (rho_+, S): the extrapolated ghosts act at

@@ -219,3 +219,33 @@ def test_aretakis_charge_drift_of_reduced_weights_on_the_slices():
         hz = gather(wprec)
         assert _rel(hz, ref) <= bound, (wprec, _rel(hz, ref))
         assert _rel(hz[:, :, 4:], ref[:, :, 4:]) <= bound, (wprec, "charge")
+
+
+def test_weno_keeps_the_horizon_charge_better_than_fd6_ko8():
+    """Sec. 4's comparison on the paper's own run: the Aretakis charge on the
+    extremal horizon (conserved in the continuum) drifts less with WENO5 than
+    with the FD6 + Kreiss-Oliger scheme at the paper's sigma = 0.01 on the
+    same grid (measured on GB300 at 4096 x 32, tau = 50 -> 300: 34% against
+    51%); both keep Phi ~ tau^-1 on the horizon."""
+    wl = I.EXTREMAL_GRAV_HYP.with_(nr=4096, nth=32)
+    drift = {}
+    for name, over in (("weno5", dict(wprec="fp32")),
+                       ("fd6_ko8", dict(wprec="fp64", scheme=1, ko_sigma=0.01))):
+        h = T.teuk_create(T.params_from_workload(wl, **over))
+        T.teuk_set_state(h, I.initial_data(wl), 0.0)
+        _, dt, _ = T.teuk_get_info(h)
+        n = int(round(5.0 / dt))
+        ts, phi, dphi, t = [], [], [], 0.0
+        while t < 300.0:
+            T.teuk_step(h, n)
+            _, hz, t = T.teuk_observe(h, wl.S)
+            ts.append(t)
+            phi.append(hz[wl.nth // 2, 0])
+            dphi.append(hz[wl.nth // 2, 4])
+        h.close()
+        ts, phi, dphi = map(np.array, (ts, phi, dphi))
+        i50, i100, i200 = (int(np.argmin(np.abs(ts - x))) for x in (50.0, 100.0, 200.0))
+        p = np.log(phi[i200] / phi[i100]) / np.log(ts[i200] / ts[i100])
+        assert abs(p + 1.0) < 0.1, (name, p)
+        drift[name] = abs(dphi[-1] / dphi[i50] - 1.0)
+    assert drift["weno5"] < 0.8 * drift["fd6_ko8"], drift

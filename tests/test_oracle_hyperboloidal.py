@@ -284,3 +284,23 @@ def test_aretakis_laws_on_the_extremal_horizon():
         assert abs(np.log(p2 / p1) / np.log(t2 / t1) + 1.0) < 0.15, (nr, seen)
         drift.append(abs(seen[2][2] / seen[0][2] - 1.0))
     assert drift[1] < 0.75 * drift[0], drift
+
+
+def test_fd6_ko8_with_extrapolated_ghosts():
+    """The comparison scheme on the hyperboloidal grid (Sec. 3.1.1): with the
+    quartic ghost extension the sixth-order derivative is exact for degree <= 4
+    at every node, edges included, and the Kreiss-Oliger eighth difference of
+    such data vanishes everywhere; in the interior the derivative stays exact
+    to degree 6."""
+    n, h = 30, 0.1
+    x = np.arange(n) * h
+    for deg in range(5):
+        f = (x - 1.3) ** deg
+        D, Q = o.fd6_ko8_1d(f, h, sigma=0.5, bc=2)
+        ex = deg * (x - 1.3) ** (deg - 1) if deg else 0 * x
+        assert np.max(np.abs(D - ex)) < 1e-9 * max(1.0, np.max(np.abs(ex))), deg
+        assert np.max(np.abs(Q)) < 1e-9, deg
+    f = (x - 1.3) ** 6
+    D, Q = o.fd6_ko8_1d(f, h, sigma=0.5, bc=2)
+    assert np.max(np.abs(D[4:n - 4] - 6 * (x[4:n - 4] - 1.3) ** 5)) < 1e-8
+    assert max(abs(D[0] - 6 * (x[0] - 1.3) ** 5), abs(Q[0])) > 1e-6

@@ -162,7 +162,7 @@ def test_theta_weno_option_on_spin_weighted_harmonics(case, a):
     assert errs[-1] < 1e-5 * abs(lam) + 1e-9
 
 
-@pytest.mark.parametrize("scheme,coords", [(0, 0), (1, 0), (0, 1)])
+@pytest.mark.parametrize("scheme,coords", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_assembly_matches_printed_real_matrices(scheme, coords):
     """F = -(M du/dx + L u + A u) with M, A, L exactly as printed in Sec. 2.3,
     using m31 = -Re K, m32 = Im K, a31 = -Re C, a32 = Im C, a33 = -Re Bt,
