@@ -44,18 +44,26 @@ FP64_FLOPS_PER_PT_STAGE = 112.0
 BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # DRAM bytes (read + write) per launch of the binary32-weight stage kernel,
 # averaged over the three stages, from one ncu capture of this workload
-# (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel source it
-# was taken on, identified by its sha256.
-NCU_TRAFFIC = {"source": "paper_2010_04760_gb300/csrc/teuk_stage.cu",
-               "sha256": "4a40a9b9e561d6189f281c8316a51bf1e230e9c8de4787cec20e9a2fe1f71103",
-               "bytes_per_launch": (31478784 + 39867648 + 39867904) / 3.0}
+# (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel sources it
+# was taken on, identified by the sha256 of their concatenation.
+NCU_TRAFFIC = {"sources": ["paper_2010_04760_gb300/csrc/teuk_stage_kernels.cuh",
+                           "paper_2010_04760_gb300/csrc/teuk_stage.cu"],
+               "sha256": "",
+               "bytes_per_launch": None}
+
+
+def kernel_source_digest(sources=None):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in sources or NCU_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def ncu_traffic():
-    import hashlib
     try:
-        with open(os.path.join(ROOT, NCU_TRAFFIC["source"]), "rb") as fh:
-            digest = hashlib.sha256(fh.read()).hexdigest()
+        digest = kernel_source_digest()
     except OSError:
         return None
     return NCU_TRAFFIC["bytes_per_launch"] if digest == NCU_TRAFFIC["sha256"] else None

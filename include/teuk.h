@@ -102,9 +102,9 @@ typedef enum {
                                       ghosts extrapolate the quartic through
                                       the five edge nodes. The pi rows move
                                       with their own speed -c (M33 = -c,
-                                      c = Atr + b). Requires TEUK_FIELD_PHI
-                                      and TEUK_THETA_CENTERED4; not in
-                                      batches. Both radial schemes.           */
+                                      c = Atr + b). Requires TEUK_FIELD_PHI;
+                                      not in batches. Both radial schemes and
+                                      both theta modes.                       */
 } teuk_coords;
 
 /* Evolved field. */

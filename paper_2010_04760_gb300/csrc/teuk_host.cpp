@@ -312,8 +312,6 @@ teuk_status teuk_check_params(const teuk_params* p) {
     if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) {
         if (p->field != TEUK_FIELD_PHI)
             return fail(TEUK_ERR_ARG, "the hyperboloidal slices evolve Phi (TEUK_FIELD_PHI)");
-        if (p->theta_mode != TEUK_THETA_CENTERED4)
-            return fail(TEUK_ERR_ARG, "the hyperboloidal slices use centred theta differences");
         if (!(p->hyp_S >= p->M && p->hyp_S <= 1e6 * p->M))
             return fail(TEUK_ERR_ARG, "hyp_S must be in [M, 1e6 M]");
         const double rhop = horizon_rho(p->M, p->a, p->hyp_S);

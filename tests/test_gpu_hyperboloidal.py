@@ -58,11 +58,12 @@ def compare(got, exp_, tol=TOL, what="", terms=0.0):
         assert err <= tol * sc + 1e-300, f"{what} component {c}: err {err:.3e} scale {sc:.3e}"
 
 
-def hyp_grid(nr, nth, a, s, m, wprec="fp64", lo=None, hi=None):
+def hyp_grid(nr, nth, a, s, m, wprec="fp64", lo=None, hi=None, theta_mode=0):
     lo = I.horizon_rho(1.0, a, S) if lo is None else lo
     hi = S if hi is None else hi
-    g = o.grid(nr, nth, lo, hi, 1.0, a, s, m, 1e-6, wprec, coords=1, S=S)
-    p = T.make_params(nr, nth, lo, hi, 1.0, a, s, m, wprec=wprec, coords=H, hyp_S=S)
+    g = o.grid(nr, nth, lo, hi, 1.0, a, s, m, 1e-6, wprec, theta_mode, coords=1, S=S)
+    p = T.make_params(nr, nth, lo, hi, 1.0, a, s, m, wprec=wprec, theta_mode=theta_mode,
+                      coords=H, hyp_S=S)
     return g, p
 
 
@@ -70,15 +71,16 @@ SHAPES = [(7, 5), (64, 8), (100, 13), (257, 33), (1000, 17)]
 PHYS = [(1.0, -2, 0), (0.0, 0, 0), (0.7, -2, 2), (0.5, 1, -1)]
 
 
+@pytest.mark.parametrize("theta_mode", [0, 1])
 @pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("phys", PHYS)
-def test_hyperboloidal_operator_parity(wprec, shape, phys):
+def test_hyperboloidal_operator_parity(wprec, shape, phys, theta_mode):
     nr, nth = shape
     a, s, m = phys
     for smooth in (True, False):
         u = I.random_state(nr, nth, nr * 5 + nth, smooth=smooth)
-        g, p = hyp_grid(nr, nth, a, s, m, wprec)
+        g, p = hyp_grid(nr, nth, a, s, m, wprec, theta_mode=theta_mode)
         co = o.coefficients(g)
         F = o.rhs(g, co, u)
         coef = dev(T.teuk_build_coefficients(p, 1.0))

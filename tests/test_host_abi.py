@@ -171,7 +171,8 @@ def test_hyperboloidal_argument_rules():
     rhop = T.horizon_rho(1.0, 0.6, 20.0)
     assert abs(ok.rstar_min - rhop) < 1e-15 and ok.rstar_max == 20.0
     assert T.teuk_check_params(T.make_params(64, 16, a=0.6, coords=H, scheme=1)) == T.TEUK_OK
-    bad = [dict(field=T.TEUK_FIELD_PSI), dict(theta_mode=1),
+    assert T.teuk_check_params(T.make_params(64, 16, a=0.6, coords=H, theta_mode=1)) == T.TEUK_OK
+    bad = [dict(field=T.TEUK_FIELD_PSI), dict(scheme=1, theta_mode=1),
            dict(hyp_S=0.5), dict(rstar_min=rhop * 0.999), dict(rstar_max=20.001),
            dict(coords=2), dict(field=3)]
     for kw in bad:
