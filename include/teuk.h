@@ -102,9 +102,9 @@ typedef enum {
                                       ghosts extrapolate the quartic through
                                       the five edge nodes. The pi rows move
                                       with their own speed -c (M33 = -c,
-                                      c = Atr + b). Requires TEUK_FIELD_PHI;
-                                      not in batches. Both radial schemes and
-                                      both theta modes.                       */
+                                      c = Atr + b). Requires TEUK_FIELD_PHI.
+                                      Both radial schemes and both theta
+                                      modes; batches too.                     */
 } teuk_coords;
 
 /* Evolved field. */
@@ -325,13 +325,13 @@ teuk_status teuk_state_dev(teuk_handle* h, double** u_dev);
 /* ---- batched evolutions ---------------------------------------------------
  * Many independent evolutions (uneven grids, spins, modes, time steps) advanced
  * together: each Runge-Kutta stage of all members is one persistent launch over
- * a device work list of (member, 4-row block, r* segment) tiles, and the steps
+ * a device work list of (member, 4-row block, radial segment) tiles, and the steps
  * are replayed from a captured CUDA graph. The launch boundary orders the
  * stages (no device-side waits). Every member runs the stage operator of
  * teuk_stage_dev (Sec. 2.3, 3.1, 3.2) with its own coefficients and dt. */
 
-/* n members with parameters ps[0..n-1] (all with the same wprec and
- * theta_mode, SSP-RK(3,3), WENO5; dt == 0 takes each member's own stability
+/* n members with parameters ps[0..n-1] (all with the same wprec, theta_mode
+ * and coords, SSP-RK(3,3), WENO5; dt == 0 takes each member's own stability
  * rule). State starts at
  * zero, t = 0. autotune != 0 times the tile shapes (32- or 64-node segments)
  * and grid sizes (4 or 8 CTAs per SM) on a synthetic state and keeps the

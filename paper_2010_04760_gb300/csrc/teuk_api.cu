@@ -286,8 +286,9 @@ static cudaError_t batch_launch_step(teuk_batch* b) {
     const int grid = b->sms * b->ctas;
     cudaError_t e = cudaSuccess;
     for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage)
-        e = launch_batch_stage(b->wprec, b->p[0].theta_mode, stage, b->seg, b->desc, b->n,
-                               b->items, grid, b->stream);
+        e = launch_batch_stage(b->wprec, b->p[0].theta_mode,
+                               b->p[0].coords == TEUK_COORDS_HYPERBOLOIDAL, stage, b->seg,
+                               b->desc, b->n, b->items, grid, b->stream);
     return e;
 }
 
@@ -310,12 +311,11 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
     for (int k = 0; k < n; ++k) {
         teuk_status st = teuk_check_params(&ps[k]);
         if (st != TEUK_OK) return fail(st, "member " + std::to_string(k) + ": " + teuk_last_error());
-        if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode)
-            return fail(TEUK_ERR_ARG, "all members need the same wprec and theta_mode");
+        if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode ||
+            ps[k].coords != ps[0].coords)
+            return fail(TEUK_ERR_ARG, "all members need the same wprec, theta_mode and coords");
         if (ps[k].rk != TEUK_RK_SSP33 || ps[k].scheme != TEUK_SCHEME_WENO5)
             return fail(TEUK_ERR_ARG, "batched evolutions use WENO5 and SSP-RK(3,3)");
-        if (ps[k].coords != TEUK_COORDS_RSTAR)
-            return fail(TEUK_ERR_ARG, "batched evolutions use r* coordinates");
     }
     teuk_batch* b = new teuk_batch();
     b->n = n;

@@ -73,7 +73,8 @@ cudaError_t launch_rk104_combine(const double* u, const double* v, double* q, do
                                  long long n, cudaStream_t st);
 cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_desc,
                               long long* items_out, cudaStream_t st);
-cudaError_t launch_batch_stage(int wprec, int theta, int stage, int segv, const void* d_desc,
-                               int n, long long items, int grid, cudaStream_t st);
+cudaError_t launch_batch_stage(int wprec, int theta, bool hyp, int stage, int segv,
+                               const void* d_desc, int n, long long items, int grid,
+                               cudaStream_t st);
 }  // namespace teuk
 #endif

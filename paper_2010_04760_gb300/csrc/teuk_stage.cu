@@ -143,36 +143,20 @@ cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_des
 
 size_t batch_desc_bytes(int n) { return sizeof(BatchDesc) * (size_t)n; }
 
-template <int W, int THETA, int SEGV>
-static cudaError_t launch_batch_wts(int stage, const BatchDesc* d, int n, long long items,
-                                    int grid, cudaStream_t st) {
-    const dim3 block(WARPS * 32);
-    switch (stage) {
-    case 1: batch_stage_kernel<W, 1, THETA, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
-    case 2: batch_stage_kernel<W, 2, THETA, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
-    default: batch_stage_kernel<W, 3, THETA, SEGV><<<grid, block, 0, st>>>(d, n, items); break;
-    }
-    return cudaGetLastError();
-}
-
-template <int W>
-static cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, int n,
-                                  long long items, int grid, cudaStream_t st) {
-    if (theta == TEUK_THETA_WENO5)
-        return segv == 64 ? launch_batch_wts<W, TEUK_THETA_WENO5, 64>(stage, d, n, items, grid, st)
-                          : launch_batch_wts<W, TEUK_THETA_WENO5, 32>(stage, d, n, items, grid, st);
-    return segv == 64 ? launch_batch_wts<W, TEUK_THETA_CENTERED4, 64>(stage, d, n, items, grid, st)
-                      : launch_batch_wts<W, TEUK_THETA_CENTERED4, 32>(stage, d, n, items, grid, st);
-}
-
-cudaError_t launch_batch_stage(int wprec, int theta, int stage, int segv, const void* d_desc,
-                               int n, long long items, int grid, cudaStream_t st) {
+cudaError_t launch_batch_stage(int wprec, int theta, bool hyp, int stage, int segv,
+                               const void* d_desc, int n, long long items, int grid,
+                               cudaStream_t st) {
     const BatchDesc* d = static_cast<const BatchDesc*>(d_desc);
+    if (hyp) return launch_batch_stage_hyp(wprec, theta, stage, segv, d, n, items, grid, st);
     switch (wprec) {
-    case TEUK_W_FP64: return launch_batch_w<TEUK_W_FP64>(stage, segv, theta, d, n, items, grid, st);
-    case TEUK_W_FP32: return launch_batch_w<TEUK_W_FP32>(stage, segv, theta, d, n, items, grid, st);
-    case TEUK_W_FP16: return launch_batch_w<TEUK_W_FP16>(stage, segv, theta, d, n, items, grid, st);
-    default: return launch_batch_w<TEUK_W_BF16>(stage, segv, theta, d, n, items, grid, st);
+    case TEUK_W_FP64:
+        return launch_batch_w<TEUK_W_FP64, false>(stage, segv, theta, d, n, items, grid, st);
+    case TEUK_W_FP32:
+        return launch_batch_w<TEUK_W_FP32, false>(stage, segv, theta, d, n, items, grid, st);
+    case TEUK_W_FP16:
+        return launch_batch_w<TEUK_W_FP16, false>(stage, segv, theta, d, n, items, grid, st);
+    default:
+        return launch_batch_w<TEUK_W_BF16, false>(stage, segv, theta, d, n, items, grid, st);
     }
 }
 

@@ -614,7 +614,7 @@ struct BatchDesc {
     unsigned eps_mant, pole_flip;
 };
 
-template <int W, int STAGE, int THETA, int SEGV>
+template <int W, int STAGE, int THETA, int SEGV, bool HYP = false>
 __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, int n,
                                                long long items) {
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
@@ -642,7 +642,7 @@ __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, 
             if (STAGE == 1) { A.un = nullptr; A.up = d.u; A.out = w1; A.alpha = 0.0; A.beta = 1.0; }
             if (STAGE == 2) { A.un = d.u; A.up = w1; A.out = w2; A.alpha = 0.75; A.beta = 0.25; }
             if (STAGE == 3) { A.un = d.u; A.up = w2; A.out = d.u; A.alpha = 1.0 / 3.0; A.beta = 2.0 / 3.0; }
-            process_segment<W, STAGE, THETA, SEGV>(A, sm[warp], lane, j, seg_blk);
+            process_segment<W, STAGE, THETA, SEGV, 0, HYP>(A, sm[warp], lane, j, seg_blk);
         }
         __syncwarp();
     }
@@ -696,8 +696,35 @@ cudaError_t launch_stage_wt(const StageArgs& A, int stage, cudaStream_t st) {
 }
 
 
-// Hyperboloidal-slice stage kernels (teuk_stage_hyp.cu).
+template <int W, int THETA, int SEGV, bool HYP>
+cudaError_t launch_batch_wts(int stage, const BatchDesc* d, int n, long long items, int grid,
+                             cudaStream_t st) {
+    const dim3 block(WARPS * 32);
+    switch (stage) {
+    case 1: batch_stage_kernel<W, 1, THETA, SEGV, HYP><<<grid, block, 0, st>>>(d, n, items); break;
+    case 2: batch_stage_kernel<W, 2, THETA, SEGV, HYP><<<grid, block, 0, st>>>(d, n, items); break;
+    default: batch_stage_kernel<W, 3, THETA, SEGV, HYP><<<grid, block, 0, st>>>(d, n, items); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int W, bool HYP>
+cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, int n,
+                           long long items, int grid, cudaStream_t st) {
+    if (theta == TEUK_THETA_WENO5)
+        return segv == 64
+                   ? launch_batch_wts<W, TEUK_THETA_WENO5, 64, HYP>(stage, d, n, items, grid, st)
+                   : launch_batch_wts<W, TEUK_THETA_WENO5, 32, HYP>(stage, d, n, items, grid, st);
+    return segv == 64
+               ? launch_batch_wts<W, TEUK_THETA_CENTERED4, 64, HYP>(stage, d, n, items, grid, st)
+               : launch_batch_wts<W, TEUK_THETA_CENTERED4, 32, HYP>(stage, d, n, items, grid, st);
+}
+
+// Hyperboloidal-slice kernels, single evolution and batches (teuk_stage_hyp.cu).
 cudaError_t launch_stage_hyp(const StageArgs& A, int wprec, int theta, int stage,
                              cudaStream_t st);
+cudaError_t launch_batch_stage_hyp(int wprec, int theta, int stage, int segv,
+                                   const BatchDesc* d, int n, long long items, int grid,
+                                   cudaStream_t st);
 
 }  // namespace teuk

@@ -68,6 +68,29 @@ def test_batch_theta_weno_members_equal_single_runs():
         np.testing.assert_array_equal(got, _single(w, ps[k], dt, 7))
 
 
+HYP_MEMBERS = [I.EXTREMAL_GRAV_HYP.with_(nr=700, nth=16, seed=21),
+               I.EXTREMAL_GRAV_HYP.with_(nr=257, nth=9, a=0.6, s=0, m=1, ells=(1,),
+                                         rs_min=I.horizon_rho(1.0, 0.6, 20.0), seed=22),
+               I.EXTREMAL_GRAV_HYP.with_(nr=1500, nth=24, a=0.3, s=-1, m=2, ells=(2,),
+                                         rs_min=I.horizon_rho(1.0, 0.3, 20.0), seed=23)]
+
+
+@pytest.mark.parametrize("theta_mode", [0, 1])
+def test_batch_of_hyperboloidal_members_equal_single_runs(theta_mode):
+    """Members on the hyperboloidal slices (the pi rows' own speed, quartic
+    ghosts at the horizon and scri) advance in one batch exactly as alone."""
+    ps = [T.params_from_workload(w, wprec="fp32", theta_mode=theta_mode) for w in HYP_MEMBERS]
+    b = T.teuk_batch_create(ps, autotune=True)
+    for k, w in enumerate(HYP_MEMBERS):
+        T.teuk_batch_set_state(b, k, I.initial_data(w), 0.0)
+    T.teuk_batch_step(b, 21)
+    for k, w in enumerate(HYP_MEMBERS):
+        dt, t, _, _ = T.teuk_batch_get_info(b, k)
+        assert abs(t - 21 * dt) < 1e-12
+        got, _ = T.teuk_batch_get_state(b, k)
+        np.testing.assert_array_equal(got, _single(w, ps[k], dt, 21))
+
+
 def test_batch_member_matches_oracle():
     w = MEMBERS[4]
     ps = [T.params_from_workload(x, wprec="fp32") for x in MEMBERS]
