@@ -133,4 +133,18 @@ def test_uneven_batch_of_64_evolutions():
         dt, _, _, _ = T.teuk_batch_get_info(b, k)
         got, _ = T.teuk_batch_get_state(b, k)
         np.testing.assert_array_equal(got, _single(wls[k], ps[k], dt, 2))
+    # one full-size member against the oracle, every node
+    k = 31
+    w = wls[k]
+    dt, _, _, _ = T.teuk_batch_get_info(b, k)
+    got, _ = T.teuk_batch_get_state(b, k)
     b.close()
+    g = o.grid(w.nr, w.nth, w.rs_min, w.rs_max, w.M, w.a, w.s, w.m, w.eps, "fp32")
+    co = o.coefficients(g)
+    u0 = I.initial_data(w)
+    exp_ = o.rk3_step(g, co, dt, u0, 2)
+    h = (w.rs_max - w.rs_min) / (w.nr - 1)
+    terms = dt * np.max(co[0]) * np.max(np.abs(u0)) / h
+    for c in range(4):
+        sc = max(np.max(np.abs(exp_[c])), terms)
+        assert np.max(np.abs(got[c] - exp_[c])) <= 1e-12 * sc, (k, w.nr, w.nth, c)

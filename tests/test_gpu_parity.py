@@ -389,3 +389,25 @@ def test_async_host_copies_and_pipelined_handles():
     assert T.teuk_get_info(hs[0])[2] == 4.5
     with pytest.raises(ValueError):
         T.teuk_get_state_async(hs[0], np.empty((4, wl.nth, wl.nr), dtype=np.float32))
+
+
+@pytest.mark.parametrize("wprec", ["fp32", "fp64"])
+def test_benchmark_launch_configuration_against_oracle(wprec):
+    """Exactly what bench.py times: the 2048 x 128 Kerr workload through a
+    handle, the handle's own time step, one teuk_step call per step (the
+    stage kernels launched with programmatic dependent launch); three steps,
+    every node against the oracle."""
+    wl = I.KERR_GRAV
+    p = T.params_from_workload(wl, wprec=wprec)
+    h = T.teuk_create(p)
+    u0 = I.initial_data(wl)
+    T.teuk_set_state(h, u0, 0.0)
+    for _ in range(3):
+        T.teuk_step(h, 1)
+    got, t = T.teuk_get_state(h)
+    _, dt, _ = T.teuk_get_info(h)
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec)
+    co = o.coefficients(g)
+    compare(got, o.rk3_step(g, co, dt, u0, 3), what=f"bench configuration {wprec}",
+            terms=term_scale(u0, dt, g, co))
+    assert abs(t - 3 * dt) < 1e-12
