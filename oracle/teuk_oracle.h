@@ -21,9 +21,11 @@
  * 4 = the reduced-precision reading carried out in binary64 (used only to show
  * that the reading is the paper's formula rearranged).
  *
- * Parity status: every routine is pinned by a test in tests/test_oracle_pins.py
- * except the Aretakis-charge interpretation of the horizon gather, which is
- * "parity unpinned" (the extremal horizon is not on an r* grid).
+ * Parity status: every routine is pinned by the tests in tests/test_oracle_pins.py,
+ * tests/test_oracle_physics.py and tests/test_oracle_hyperboloidal.py, except the
+ * Aretakis-charge interpretation of the horizon gather in r*, which is "parity
+ * unpinned" (the extremal horizon is not on an r* grid). On the hyperboloidal
+ * grid the horizon is node 0 and the Aretakis laws are pinned.
  */
 #ifndef TEUK_ORACLE_H
 #define TEUK_ORACLE_H

@@ -26,7 +26,6 @@ TEUK_SCHEME_WENO5, TEUK_SCHEME_FD6_KO8 = 0, 1
 TEUK_COORDS_RSTAR, TEUK_COORDS_HYPERBOLOIDAL = 0, 1
 TEUK_FIELD_PSI, TEUK_FIELD_PHI = 0, 1
 WPREC = {"fp64": TEUK_W_FP64, "fp32": TEUK_W_FP32, "fp16": TEUK_W_FP16, "bf16": TEUK_W_BF16}
-COEF_PLANES = 11
 
 
 class TeukError(RuntimeError):
