@@ -249,3 +249,30 @@ def test_weno_keeps_the_horizon_charge_better_than_fd6_ko8():
         assert abs(p + 1.0) < 0.1, (name, p)
         drift[name] = abs(dphi[-1] / dphi[i50] - 1.0)
     assert drift["weno5"] < 0.8 * drift["fd6_ko8"], drift
+
+
+def test_quasinormal_ringing_at_scri_on_gpu():
+    """The CUDA path (binary32 weights, handle, observation at scri) rings at
+    the textbook fundamental quasinormal frequencies of
+    tests/golden/qnm_frequencies.txt (Schwarzschild scalar and gravitational
+    l = 2; Kerr a = 0.7 and 0.9, (l, m) = (2, 2), s = -2): Phi at scri
+    projected on sY_lm, Prony fit of order 6 over tau = 70..120 M; |omega|
+    within 0.5%, gamma within 1%."""
+    from _qnm import golden_qnm, nearest_mode, prony_modes
+    for s, l, m, a, wr, gam in golden_qnm():
+        wl = I.EXTREMAL_GRAV_HYP.with_(nr=1024, nth=16, a=a, s=s, m=m, ells=(l,), rc=4.0,
+                                       width=0.5, rs_min=I.horizon_rho(1.0, a, 20.0))
+        h = T.teuk_create(T.params_from_workload(wl, dt=0.25 / 100))
+        T.teuk_set_state(h, I.initial_data(wl), 0.0)
+        th = I.theta_nodes(wl.nth)
+        w = I.swsh(s, l, m, th) * np.sin(th) * (np.pi / wl.nth)
+        ts, ys = [], []
+        for _ in range(500):
+            T.teuk_step(h, 100)
+            wave, _, t = T.teuk_observe(h, wl.S)
+            ts.append(t)
+            ys.append(np.sum(w * (wave[:, 0] + 1j * wave[:, 1])))
+        h.close()
+        g, om = nearest_mode(prony_modes(np.array(ts), np.array(ys), 70.0, 120.0), wr, gam)
+        assert abs(abs(om) - wr) < 5e-3 * wr, (s, l, m, a, om, wr)
+        assert abs(g - gam) < 1e-2 * gam, (s, l, m, a, g, gam)
