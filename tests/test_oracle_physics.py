@@ -258,3 +258,39 @@ def test_price_tail_exponent_schwarzschild_l0():
     p = ts[1:-1] * (ps[2:] - ps[:-2]) / (ts[2:] - ts[:-2]) / ps[1:-1]
     late = (ts[1:-1] > 250.0)
     assert np.all(np.abs(p[late] + 3.0) < 0.1), p[late]
+
+
+def test_quasinormal_ringing_in_rstar():
+    """The r* system (BL time, field Phi = r Delta^s Psi) rings at the textbook
+    fundamental quasinormal frequencies of tests/golden/qnm_frequencies.txt
+    at r* = 50 M: Schwarzschild and Kerr a = 0.7, (l, m) = (2, 2), s = -2;
+    Prony fit of order 6 of the sY_lm projection over t = 120..170 M (the
+    boundaries at -100 M and 300 M are causally disconnected from it);
+    |omega| within 0.5%, gamma within 1%."""
+    from _qnm import golden_qnm, nearest_mode, prony_modes
+    nr, nth, every = 1024, 16, 0.25
+    h = 400.0 / (nr - 1)
+    dth = np.pi / nth
+    for s, l, m, a, wr, gam in golden_qnm():
+        if s != -2 or a > 0.8:
+            continue
+        g = o.grid(nr, nth, -100.0, 300.0, 1.0, a, s, m, field=1)
+        co = o.coefficients(g)
+        kap = co[7] * 16 / 3 / dth ** 2 + np.abs(co[8]) * 1.5 / dth + np.hypot(co[5], co[6])
+        dt = 0.5 / np.max(co[0] / h + np.sqrt(np.maximum(kap, 0.0)))
+        n = int(np.ceil(every / dt))
+        dt = every / n
+        wl = I.KERR_GRAV.with_(nr=nr, nth=nth, a=a, s=s, m=m, ells=(l,), rc=30.0, width=3.0)
+        u = I.initial_data(wl)
+        th = I.theta_nodes(nth)
+        w = I.swsh(s, l, m, th) * np.sin(th) * dth
+        ie = int(round(150.0 / h))                       # r* = 50 M
+        ts, ys, t = [], [], 0.0
+        while t < 175.0:
+            u = o.rk3_step(g, co, dt, u, n)
+            t += n * dt
+            ts.append(t)
+            ys.append(np.sum(w * (u[0, :, ie] + 1j * u[1, :, ie])))
+        gm, om = nearest_mode(prony_modes(np.array(ts), np.array(ys), 120.0, 170.0), wr, gam)
+        assert abs(abs(om) - wr) < 5e-3 * wr, (a, om, wr)
+        assert abs(gm - gam) < 1e-2 * gam, (a, gm, gam)
