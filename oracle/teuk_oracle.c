@@ -6,7 +6,7 @@
  * library. Every routine follows the paper's steps in the paper's order, with
  * plain loops; the passage each one follows is cited beside it.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Coordinates (coords 0): Boyer-Lindquist time t, tortoise r*, ingoing
  *    azimuth phi~ (Sec. 2.2). coords 1: the paper's hyperboloidal slices
  *    (tau, rho) of Sec. 2.2, whose coefficients (Eq. near_final) the paper
