@@ -411,3 +411,21 @@ def test_benchmark_launch_configuration_against_oracle(wprec):
     compare(got, o.rk3_step(g, co, dt, u0, 3), what=f"bench configuration {wprec}",
             terms=term_scale(u0, dt, g, co))
     assert abs(t - 3 * dt) < 1e-12
+
+
+def test_plain_c_client_steps_and_observes(tmp_path):
+    """The C client (tests/c/teuk_c_client.c) drives a handle through the C ABI
+    alone: seeded Gaussian data, 40 steps, observation, a bitwise checkpoint
+    round trip, and a status for a bad call; its observation equals the same
+    sequence issued through the Python binding."""
+    import test_host_abi as H
+    got = H._c_client(tmp_path)("gpu")
+    assert got["restart_bitwise"] == "1"
+    assert int(got["neg_steps_status"]) == T.TEUK_ERR_ARG
+    p = T.params_from_workload(I.KERR_GRAV, wprec="fp32")
+    h = T.teuk_create(p)
+    T.teuk_set_gaussian(h, 30.0, 3.0, [1.0 + 0.5j])
+    T.teuk_step(h, 40)
+    wave, _, t = T.teuk_observe(h, 50.0)
+    assert float(got["t"]) == t
+    assert float(got["wave_abs_sum"]) == float(np.abs(wave).sum())

@@ -226,3 +226,41 @@ def test_params_struct_layout_matches_the_header(tmp_path):
     for n in names:
         assert int(got[n]) == getattr(T.teuk_params, n).offset, n
     assert int(got["sizeof"]) == ctypes.sizeof(T.teuk_params)
+
+
+def _c_client(tmp_path):
+    """Builds tests/c/teuk_c_client.c against include/teuk.h and libteuk.so."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(T.LIB_PATH)
+    exe = str(tmp_path / "teuk_c_client")
+    subprocess.check_call([cc, "-O2", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c", "teuk_c_client.c"), "-o", exe,
+                           "-L", libdir, "-lteuk", "-lm", "-Wl,-rpath," + libdir])
+    env = dict(os.environ)
+    env["LD_LIBRARY_PATH"] = os.pathsep.join(
+        [p for p in ("/usr/local/cuda/lib64", env.get("LD_LIBRARY_PATH", "")) if p])
+
+    def run(*args):
+        out = subprocess.run([exe, *args], capture_output=True, text=True, env=env)
+        assert out.returncode == 0, out.stderr
+        return dict(line.split(None, 1) for line in out.stdout.splitlines())
+    return run
+
+
+def test_plain_c_client_of_the_abi(tmp_path):
+    """A C program using only include/teuk.h gets the same time step and
+    coefficient array as the Python binding, and a status (with a message)
+    for an invalid parameter set."""
+    got = _c_client(tmp_path)()
+    p = T.params_from_workload(I.KERR_GRAV, wprec="fp32")
+    dt = T.teuk_stable_dt(p)
+    assert float(got["dt"]) == dt
+    assert int(got["coef_count"]) == T.teuk_coeff_count(p)
+    assert float(got["coef_abs_sum"]) == pytest.approx(np.abs(T.teuk_build_coefficients(p, dt)).sum(),
+                                                       rel=1e-12)   # summation order
+    assert int(got["bad_status"]) == T.TEUK_ERR_ARG and got["bad_message_nonempty"] == "1"
