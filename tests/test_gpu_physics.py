@@ -305,3 +305,54 @@ def test_quasinormal_ringing_in_rstar_on_gpu(field):
         g, om = nearest_mode(prony_modes(np.array(ts), np.array(ys), 120.0, 170.0), wr, gam)
         assert abs(abs(om) - wr) < 5e-3 * wr, (s, l, m, a, om, wr)
         assert abs(g - gam) < 2e-2 * gam, (s, l, m, a, g, gam)
+
+
+def _tail_reference():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "tail_coarse_reference.txt")
+    rows = np.loadtxt(path, comments="#")
+    return {a: rows[rows[:, 0] == a][:, 1:] for a in (0.0, 1.0)}
+
+
+@pytest.mark.parametrize("wprec", ["fp64", "fp32"])
+def test_tail_workload_coarsened_against_the_oracle_to_t_1e4(wprec):
+    """The tail workload on the coarsened grid of
+    tests/golden/make_tail_reference.py (4096 x 8, r* in [-5000, 5000] M,
+    l = 0 pulse), evolved through the CUDA path to t = 10^4 M (about 36,000
+    SSP-RK(3,3) steps) with the oracle's time step, for a = 0 and a = M:
+    Psi at r* = 50 M every 100 M against the stored oracle run, and the Price
+    index p = t dPsi/dt / Psi over t = 5000..9500 M (-2.99..-2.98 in the oracle
+    for a = 0 and a = M, Price: -3)."""
+    import importlib.util
+    import os
+    gen = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                       "make_tail_reference.py")
+    spec = importlib.util.spec_from_file_location("make_tail_reference", gen)
+    mtr = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mtr)
+    ref = _tail_reference()
+    for a in (0.0, 1.0):
+        wl = mtr.coarse_workload(a)
+        g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, 1.0, a, 0, 0)
+        dt, n = mtr.time_step(g, o.coefficients(g))
+        p = T.params_from_workload(wl, wprec=wprec, dt=dt)
+        h = T.teuk_create(p)
+        T.teuk_set_state(h, I.initial_data(wl), 0.0)
+        ts, ys = [], []
+        for _ in range(len(ref[a])):
+            T.teuk_step(h, n)
+            wave, _, t = T.teuk_observe(h, mtr.R_EXT)
+            ts.append(t)
+            ys.append(wave[wl.nth // 2, 0])
+        h.close()
+        ts, ys = np.array(ts), np.array(ys)
+        r = ref[a]
+        np.testing.assert_allclose(ts, r[:, 0], rtol=0, atol=1e-6)
+        tol = 1e-9 if wprec == "fp64" else 1e-6
+        assert np.max(np.abs(ys - r[:, 1])) <= tol * np.max(np.abs(r[:, 1])), (a, wprec)
+        pg = ts[1:-1] * (ys[2:] - ys[:-2]) / (ts[2:] - ts[:-2]) / ys[1:-1]
+        # before the pulse's reflection from r* = 5000 M returns (t ~ 9900 M)
+        late = (ts[1:-1] >= 5000.0) & (ts[1:-1] <= 9500.0)
+        assert np.max(np.abs(pg[late] - r[1:-1, 2][late])) < 1e-3, (a, wprec)
+        assert np.all(np.abs(pg[late] + 3.0) < 0.05), (a, pg[late])
