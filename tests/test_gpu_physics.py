@@ -354,5 +354,8 @@ def test_tail_workload_coarsened_against_the_oracle_to_t_1e4(wprec):
         pg = ts[1:-1] * (ys[2:] - ys[:-2]) / (ts[2:] - ts[:-2]) / ys[1:-1]
         # before the pulse's reflection from r* = 5000 M returns (t ~ 9900 M)
         late = (ts[1:-1] >= 5000.0) & (ts[1:-1] <= 9500.0)
-        assert np.max(np.abs(pg[late] - r[1:-1, 2][late])) < 1e-3, (a, wprec)
+        # binary32 weights add noise of about +-0.006 to the late index, where
+        # the tail is ~1e-7 of the initial pulse (measured on GB300)
+        ptol = 1e-3 if wprec == "fp64" else 1e-2
+        assert np.max(np.abs(pg[late] - r[1:-1, 2][late])) < ptol, (a, wprec)
         assert np.all(np.abs(pg[late] + 3.0) < 0.05), (a, pg[late])
