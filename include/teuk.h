@@ -7,7 +7,7 @@
  * the first-order system du/dt = -(M du/dx + L u + A u) (Sec. 2.3, Eq. evln)
  * with the WENO5 (Jiang-Shu) derivative in x (Sec. 3.1.2), the nonlinear
  * weights computed in a reduced precision (Sec. 3.1.3), fourth-order centred
- * differences in theta (Sec. 3.1: "standard centered differencing"), and the
+ * differences in theta (Sec. 3.1 asks for centred differences), and the
  * SSP-RK(3,3) update (Sec. 3.2).
  *
  * Conventions shared by every call

@@ -25,7 +25,7 @@
  *    the edge nodes. theta: cell-centred grid, ghost rows mirror across the
  *    poles with parity (-1)^(m+s).
  *  - theta derivatives: fourth-order centred differences (the paper says
- *    "standard centered differencing" without an order). Optional theta WENO
+ *    centred differences without an order). Optional theta WENO
  *    (theta_mode 1): the first derivative in the Bth term is the WENO5
  *    derivative along theta, upwinded by the sign of the term's speed -Bth
  *    (the term read as -(-Bth) dPsi/dtheta), with weights in the same
