@@ -25,7 +25,9 @@
  *  - Host pointers are read or written synchronously and stay owned by the
  *    caller. Device pointers ("_dev") are caller-owned device memory on the
  *    current CUDA device. Handles own their device memory.
- *  - Every call returns a teuk_status; nothing throws across the ABI.
+ *  - Every call returns a teuk_status; nothing throws across the ABI (a
+ *    failed host allocation returns TEUK_ERR_HOST and frees what the call
+ *    had taken).
  *    A failing call leaves its outputs unspecified and the handle usable
  *    unless the status is TEUK_ERR_CUDA.
  *  - "stream" arguments are cudaStream_t values passed as void* (NULL = the
@@ -46,8 +48,9 @@ typedef enum {
     TEUK_ERR_ARG = 1,        /* invalid argument (message via teuk_last_error) */
     TEUK_ERR_CUDA = 2,       /* a CUDA call failed                               */
     TEUK_ERR_NONFINITE = 3,  /* the state holds a NaN or an infinity             */
-    TEUK_ERR_TIMEOUT = 4,    /* a device-side wait gave up                       */
-    TEUK_ERR_STATE = 5       /* call out of order (e.g. no state set yet)        */
+    TEUK_ERR_TIMEOUT = 4,    /* reserved: no kernel of this library waits        */
+    TEUK_ERR_STATE = 5,      /* reserved: no call depends on an earlier one      */
+    TEUK_ERR_HOST = 6        /* host memory or a host thread was not available   */
 } teuk_status;
 
 /* Precision of the WENO smoothness indicators and nonlinear weights

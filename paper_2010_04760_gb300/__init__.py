@@ -18,7 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libteuk.so")
 
-TEUK_OK, TEUK_ERR_ARG, TEUK_ERR_CUDA, TEUK_ERR_NONFINITE, TEUK_ERR_TIMEOUT, TEUK_ERR_STATE = range(6)
+(TEUK_OK, TEUK_ERR_ARG, TEUK_ERR_CUDA, TEUK_ERR_NONFINITE, TEUK_ERR_TIMEOUT, TEUK_ERR_STATE,
+ TEUK_ERR_HOST) = range(7)
 TEUK_W_FP64, TEUK_W_FP32, TEUK_W_FP16, TEUK_W_BF16 = range(4)
 TEUK_THETA_CENTERED4, TEUK_THETA_WENO5 = 0, 1
 TEUK_RK_SSP33, TEUK_RK_SSP104 = 0, 1

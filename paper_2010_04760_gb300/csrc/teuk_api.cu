@@ -169,35 +169,39 @@ extern "C" {
 teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_dev,
                            const double* u_n, const double* u_prev, double* u_out,
                            int stage, void* stream) {
-    teuk_status st = teuk_check_params(p);
-    if (st != TEUK_OK) return st;
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
-    if (stage < 0 || stage > 3) return fail(TEUK_ERR_ARG, "stage must be 0..3");
-    if (!coef_dev || !u_prev || !u_out) return fail(TEUK_ERR_ARG, "NULL device pointer");
-    if (stage >= 2 && p->rk != TEUK_RK_SSP33)
-        return fail(TEUK_ERR_ARG, "stages 2 and 3 are SSP-RK(3,3) stages");
-    if (stage >= 2 && !u_n) return fail(TEUK_ERR_ARG, "u_n is NULL for stage 2/3");
-    if (u_out == u_prev) return fail(TEUK_ERR_ARG, "u_out aliases u_prev");
-    TEUK_CUDA(launch_stage(*p, coef_dev, u_n, u_prev, u_out, stage, dt, (cudaStream_t)stream));
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_stage_dev", [&]() -> teuk_status {
+        teuk_status st = teuk_check_params(p);
+        if (st != TEUK_OK) return st;
+        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+        if (stage < 0 || stage > 3) return fail(TEUK_ERR_ARG, "stage must be 0..3");
+        if (!coef_dev || !u_prev || !u_out) return fail(TEUK_ERR_ARG, "NULL device pointer");
+        if (stage >= 2 && p->rk != TEUK_RK_SSP33)
+            return fail(TEUK_ERR_ARG, "stages 2 and 3 are SSP-RK(3,3) stages");
+        if (stage >= 2 && !u_n) return fail(TEUK_ERR_ARG, "u_n is NULL for stage 2/3");
+        if (u_out == u_prev) return fail(TEUK_ERR_ARG, "u_out aliases u_prev");
+        TEUK_CUDA(launch_stage(*p, coef_dev, u_n, u_prev, u_out, stage, dt, (cudaStream_t)stream));
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_dev,
                           double* u_dev, double* work_dev, int64_t nsteps, void* stream) {
-    NvtxRange trace("teuk_step_dev");
-    teuk_status st = teuk_check_params(p);
-    if (st != TEUK_OK) return st;
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
-    if (!coef_dev || !u_dev || !work_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
-    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
-    const size_t n = 4 * (size_t)p->nr * p->ntheta;
-    if (work_dev < u_dev + n && u_dev < work_dev + scratch_states(*p) * n)
-        return fail(TEUK_ERR_ARG, "work_dev overlaps u_dev");
-    for (int64_t k = 0; k < nsteps; ++k)
-        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, work_dev, (cudaStream_t)stream));
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_step_dev", [&]() -> teuk_status {
+        NvtxRange trace("teuk_step_dev");
+        teuk_status st = teuk_check_params(p);
+        if (st != TEUK_OK) return st;
+        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+        if (!coef_dev || !u_dev || !work_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
+        if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+        const size_t n = 4 * (size_t)p->nr * p->ntheta;
+        if (work_dev < u_dev + n && u_dev < work_dev + scratch_states(*p) * n)
+            return fail(TEUK_ERR_ARG, "work_dev overlaps u_dev");
+        for (int64_t k = 0; k < nsteps; ++k)
+            TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, work_dev, (cudaStream_t)stream));
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 // Stage buffers of teuk_step_dev_static: a fixed device array, so that the
@@ -211,69 +215,73 @@ static double* g_static_ptr[256] = {nullptr};
 
 teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* coef_dev,
                                  double* u_dev, int64_t nsteps, void* stream) {
-    teuk_status st = teuk_check_params(p);
-    if (st != TEUK_OK) return st;
-    const size_t nodes = (size_t)p->nr * p->ntheta;
-    if (nodes > (size_t)TEUK_STATIC_MAX_NODES)
-        return fail(TEUK_ERR_ARG, "grid has " + std::to_string(nodes) +
-                                      " nodes; teuk_step_dev_static holds at most " +
-                                      std::to_string(TEUK_STATIC_MAX_NODES));
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
-    if (!coef_dev || !u_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
-    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
-    if (p->rk != TEUK_RK_SSP33)
-        return fail(TEUK_ERR_ARG, "teuk_step_dev_static supports SSP-RK(3,3) only");
-    int dev = 0;
-    TEUK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return fail(TEUK_ERR_ARG, "device ordinal out of range");
-    double* stages = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_static_mutex);
-        if (!g_static_ptr[dev]) {
-            void* ptr = nullptr;
-            TEUK_CUDA(cudaGetSymbolAddress(&ptr, g_static_stages));
-            g_static_ptr[dev] = static_cast<double*>(ptr);
+    return guarded("teuk_step_dev_static", [&]() -> teuk_status {
+        teuk_status st = teuk_check_params(p);
+        if (st != TEUK_OK) return st;
+        const size_t nodes = (size_t)p->nr * p->ntheta;
+        if (nodes > (size_t)TEUK_STATIC_MAX_NODES)
+            return fail(TEUK_ERR_ARG, "grid has " + std::to_string(nodes) +
+                                          " nodes; teuk_step_dev_static holds at most " +
+                                          std::to_string(TEUK_STATIC_MAX_NODES));
+        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+        if (!coef_dev || !u_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
+        if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+        if (p->rk != TEUK_RK_SSP33)
+            return fail(TEUK_ERR_ARG, "teuk_step_dev_static supports SSP-RK(3,3) only");
+        int dev = 0;
+        TEUK_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 256) return fail(TEUK_ERR_ARG, "device ordinal out of range");
+        double* stages = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(g_static_mutex);
+            if (!g_static_ptr[dev]) {
+                void* ptr = nullptr;
+                TEUK_CUDA(cudaGetSymbolAddress(&ptr, g_static_stages));
+                g_static_ptr[dev] = static_cast<double*>(ptr);
+            }
+            stages = g_static_ptr[dev];
         }
-        stages = g_static_ptr[dev];
-    }
-    for (int64_t k = 0; k < nsteps; ++k)
-        TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, stages, (cudaStream_t)stream));
-    clear_error();
-    return TEUK_OK;
+        for (int64_t k = 0; k < nsteps; ++k)
+            TEUK_CUDA(launch_step(*p, coef_dev, dt, u_dev, stages, (cudaStream_t)stream));
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_fp64_fma_rate(void* stream, double* fma_per_s) {
-    if (!fma_per_s) return fail(TEUK_ERR_ARG, "fma_per_s is NULL");
-    int dev = 0, sms = 0;
-    TEUK_CUDA(cudaGetDevice(&dev));
-    TEUK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int threads = 256, blocks = sms * 8;
-    cudaStream_t st = (cudaStream_t)stream;
-    double* out = nullptr;
-    TEUK_CUDA(cudaMalloc(&out, sizeof(double) * (size_t)threads * blocks));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float best = 0.0f;
-    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-        e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess) {
-            fp64_rate_kernel<<<blocks, threads, 0, st>>>(out, 0.999999, 1e-7);
-            e = cudaGetLastError();
+    return guarded("teuk_fp64_fma_rate", [&]() -> teuk_status {
+        if (!fma_per_s) return fail(TEUK_ERR_ARG, "fma_per_s is NULL");
+        int dev = 0, sms = 0;
+        TEUK_CUDA(cudaGetDevice(&dev));
+        TEUK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int threads = 256, blocks = sms * 8;
+        cudaStream_t st = (cudaStream_t)stream;
+        double* out = nullptr;
+        TEUK_CUDA(cudaMalloc(&out, sizeof(double) * (size_t)threads * blocks));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best = 0.0f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) {
+                fp64_rate_kernel<<<blocks, threads, 0, st>>>(out, 0.999999, 1e-7);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaFree(out);
-    if (e != cudaSuccess) return cuda_fail(e, "teuk_fp64_fma_rate");
-    *fma_per_s = 8.0 * kRateIters * (double)threads * blocks / (best * 1e-3);
-    clear_error();
-    return TEUK_OK;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(out);
+        if (e != cudaSuccess) return cuda_fail(e, "teuk_fp64_fma_rate");
+        *fma_per_s = 8.0 * kRateIters * (double)threads * blocks / (best * 1e-3);
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 static cudaError_t batch_upload(teuk_batch* b, int seg) {
@@ -304,162 +312,181 @@ teuk_status teuk_batch_destroy(teuk_batch* b) {
 
 teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int autotune,
                               teuk_batch** out) {
-    NvtxRange trace("teuk_batch_create");
-    if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!ps || n < 1) return fail(TEUK_ERR_ARG, "need n >= 1 parameter sets");
-    for (int k = 0; k < n; ++k) {
-        teuk_status st = teuk_check_params(&ps[k]);
-        if (st != TEUK_OK) return fail(st, "member " + std::to_string(k) + ": " + teuk_last_error());
-        if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode ||
-            ps[k].coords != ps[0].coords)
-            return fail(TEUK_ERR_ARG, "all members need the same wprec, theta_mode and coords");
-        if (ps[k].rk != TEUK_RK_SSP33 || ps[k].scheme != TEUK_SCHEME_WENO5)
-            return fail(TEUK_ERR_ARG, "batched evolutions use WENO5 and SSP-RK(3,3)");
-    }
-    teuk_batch* b = new teuk_batch();
-    b->n = n;
-    b->wprec = ps[0].wprec;
-    b->p.assign(ps, ps + n);
-    b->dt.resize(n);
-    b->t.assign(n, 0.0);
-    b->off.resize(n);
-    size_t total = 0, max_plane = 0;
-    for (int k = 0; k < n; ++k) {
-        teuk_status st = teuk_stable_dt(&ps[k], &b->dt[k]);
-        if (st != TEUK_OK) { delete b; return st; }
-        b->off[k] = total;
-        total += (((12 + coef_planes(ps[k])) * b->plane(k) + 31) / 32) * 32;  // aligned
-        max_plane = std::max(max_plane, b->plane(k));
-    }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) {
-        if (stream) {
-            b->stream = (cudaStream_t)stream;
-        } else {
-            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-            b->own_stream = (e == cudaSuccess);
+    return guarded("teuk_batch_create", [&]() -> teuk_status {
+        NvtxRange trace("teuk_batch_create");
+        if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        if (!ps || n < 1) return fail(TEUK_ERR_ARG, "need n >= 1 parameter sets");
+        for (int k = 0; k < n; ++k) {
+            teuk_status st = teuk_check_params(&ps[k]);
+            if (st != TEUK_OK)
+                return fail(st, "member " + std::to_string(k) + ": " + teuk_last_error());
+            if (ps[k].wprec != ps[0].wprec || ps[k].theta_mode != ps[0].theta_mode ||
+                ps[k].coords != ps[0].coords)
+                return fail(TEUK_ERR_ARG, "all members need the same wprec, theta_mode and coords");
+            if (ps[k].rk != TEUK_RK_SSP33 || ps[k].scheme != TEUK_SCHEME_WENO5)
+                return fail(TEUK_ERR_ARG, "batched evolutions use WENO5 and SSP-RK(3,3)");
         }
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&b->pool, total * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b->desc, batch_desc_bytes(n));
-    int max_planes = 0;
-    for (int k = 0; k < n; ++k) max_planes = std::max(max_planes, coef_planes(ps[k]));
-    std::vector<double> host((size_t)max_planes * max_plane);
-    for (int k = 0; k < n && e == cudaSuccess; ++k) {
-        teuk_status st = teuk_build_coefficients(&ps[k], b->dt[k], host.data());
-        if (st != TEUK_OK) { teuk_batch_destroy(b); return st; }
-        e = cudaMemcpyAsync(b->coef(k), host.data(), coef_planes(ps[k]) * b->plane(k) * sizeof(double),
-                            cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host buffer is reused
-    }
-    b->seg = b->wprec == TEUK_W_FP64 ? 64 : 32;
-    b->ctas = 8;
-    if (e == cudaSuccess && autotune) {
-        // time every (segment, CTAs per SM) candidate on a synthetic state
-        for (int k = 0; k < n && e == cudaSuccess; ++k) {
-            synth_state_kernel<<<b->sms * 4, 256, 0, b->stream>>>(b->u(k), 4 * (long long)b->plane(k));
-            e = cudaGetLastError();
+        struct Owner {             // destroys a half-built batch on any early return or throw
+            teuk_batch* b;
+            ~Owner() { if (b) teuk_batch_destroy(b); }
+        } own{new teuk_batch()};
+        teuk_batch* b = own.b;
+        b->n = n;
+        b->wprec = ps[0].wprec;
+        b->p.assign(ps, ps + n);
+        b->dt.resize(n);
+        b->t.assign(n, 0.0);
+        b->off.resize(n);
+        size_t total = 0, max_plane = 0;
+        for (int k = 0; k < n; ++k) {
+            teuk_status st = teuk_stable_dt(&ps[k], &b->dt[k]);
+            if (st != TEUK_OK) return st;
+            b->off[k] = total;
+            total += (((12 + coef_planes(ps[k])) * b->plane(k) + 31) / 32) * 32;  // aligned
+            max_plane = std::max(max_plane, b->plane(k));
         }
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (e == cudaSuccess) e = cudaEventCreate(&e0);
-        if (e == cudaSuccess) e = cudaEventCreate(&e1);
-        float best = -1.0f;
-        int best_seg = b->seg, best_ctas = b->ctas;
-        const int segs[2] = {32, 64}, ctas[2] = {4, 8};
-        for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
-            e = batch_upload(b, segs[a]);
-            for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
-                b->seg = segs[a];
-                b->ctas = ctas[c];
-                e = batch_launch_step(b);                                  // warm-up
-                if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-                for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = batch_launch_step(b);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (e == cudaSuccess && (best < 0.0f || ms < best)) {
-                    best = ms; best_seg = segs[a]; best_ctas = ctas[c];
-                }
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) {
+            if (stream) {
+                b->stream = (cudaStream_t)stream;
+            } else {
+                e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+                b->own_stream = (e == cudaSuccess);
             }
         }
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
-        b->seg = best_seg;
-        b->ctas = best_ctas;
-    }
-    for (int k = 0; k < n && e == cudaSuccess; ++k)
-        e = cudaMemsetAsync(b->u(k), 0, 4 * b->plane(k) * sizeof(double), b->stream);
-    if (e == cudaSuccess) e = batch_upload(b, b->seg);
-    if (e != cudaSuccess) {
-        teuk_batch_destroy(b);
-        return cuda_fail(e, "teuk_batch_create");
-    }
-    *out = b;
-    clear_error();
-    return TEUK_OK;
+        if (e == cudaSuccess) e = cudaMalloc(&b->pool, total * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&b->desc, batch_desc_bytes(n));
+        int max_planes = 0;
+        for (int k = 0; k < n; ++k) max_planes = std::max(max_planes, coef_planes(ps[k]));
+        std::vector<double> host((size_t)max_planes * max_plane);
+        for (int k = 0; k < n && e == cudaSuccess; ++k) {
+            teuk_status st = teuk_build_coefficients(&ps[k], b->dt[k], host.data());
+            if (st != TEUK_OK) return st;
+            e = cudaMemcpyAsync(b->coef(k), host.data(),
+                                coef_planes(ps[k]) * b->plane(k) * sizeof(double),
+                                cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host buffer is reused
+        }
+        b->seg = b->wprec == TEUK_W_FP64 ? 64 : 32;
+        b->ctas = 8;
+        if (e == cudaSuccess && autotune) {
+            // time every (segment, CTAs per SM) candidate on a synthetic state
+            for (int k = 0; k < n && e == cudaSuccess; ++k) {
+                synth_state_kernel<<<b->sms * 4, 256, 0, b->stream>>>(b->u(k),
+                                                                      4 * (long long)b->plane(k));
+                e = cudaGetLastError();
+            }
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (e == cudaSuccess) e = cudaEventCreate(&e0);
+            if (e == cudaSuccess) e = cudaEventCreate(&e1);
+            float best = -1.0f;
+            int best_seg = b->seg, best_ctas = b->ctas;
+            const int segs[2] = {32, 64}, ctas[2] = {4, 8};
+            for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+                e = batch_upload(b, segs[a]);
+                for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+                    b->seg = segs[a];
+                    b->ctas = ctas[c];
+                    e = batch_launch_step(b);                                  // warm-up
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+                    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = batch_launch_step(b);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e == cudaSuccess && (best < 0.0f || ms < best)) {
+                        best = ms; best_seg = segs[a]; best_ctas = ctas[c];
+                    }
+                }
+            }
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            b->seg = best_seg;
+            b->ctas = best_ctas;
+        }
+        for (int k = 0; k < n && e == cudaSuccess; ++k)
+            e = cudaMemsetAsync(b->u(k), 0, 4 * b->plane(k) * sizeof(double), b->stream);
+        if (e == cudaSuccess) e = batch_upload(b, b->seg);
+        if (e != cudaSuccess) return cuda_fail(e, "teuk_batch_create");
+        *out = b;
+        own.b = nullptr;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_batch_set_state(teuk_batch* b, int k, const double* u_host, double t) {
-    if (!b || !u_host || k < 0 || k >= (b ? b->n : 0)) return fail(TEUK_ERR_ARG, "bad argument");
-    TEUK_CUDA(cudaMemcpyAsync(b->u(k), u_host, 4 * b->plane(k) * sizeof(double),
-                              cudaMemcpyHostToDevice, b->stream));
-    TEUK_CUDA(cudaStreamSynchronize(b->stream));
-    b->t[k] = t;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_batch_set_state", [&]() -> teuk_status {
+        if (!b || !u_host || k < 0 || k >= b->n) return fail(TEUK_ERR_ARG, "bad argument");
+        TEUK_CUDA(cudaMemcpyAsync(b->u(k), u_host, 4 * b->plane(k) * sizeof(double),
+                                  cudaMemcpyHostToDevice, b->stream));
+        TEUK_CUDA(cudaStreamSynchronize(b->stream));
+        b->t[k] = t;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_batch_get_state(teuk_batch* b, int k, double* u_host, double* t_out) {
-    if (!b || !u_host || k < 0 || k >= (b ? b->n : 0)) return fail(TEUK_ERR_ARG, "bad argument");
-    TEUK_CUDA(cudaMemcpyAsync(u_host, b->u(k), 4 * b->plane(k) * sizeof(double),
-                              cudaMemcpyDeviceToHost, b->stream));
-    TEUK_CUDA(cudaStreamSynchronize(b->stream));
-    if (t_out) *t_out = b->t[k];
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_batch_get_state", [&]() -> teuk_status {
+        if (!b || !u_host || k < 0 || k >= b->n) return fail(TEUK_ERR_ARG, "bad argument");
+        TEUK_CUDA(cudaMemcpyAsync(u_host, b->u(k), 4 * b->plane(k) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, b->stream));
+        TEUK_CUDA(cudaStreamSynchronize(b->stream));
+        if (t_out) *t_out = b->t[k];
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_batch_step(teuk_batch* b, int64_t nsteps) {
-    NvtxRange trace("teuk_batch_step");
-    if (!b) return fail(TEUK_ERR_ARG, "batch is NULL");
-    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
-    const int kChunk = 16;
-    if (nsteps >= kChunk && !b->exec) {
-        cudaGraph_t g = nullptr;
-        TEUK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k < kChunk && e == cudaSuccess; ++k) e = batch_launch_step(b);
-        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
-        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&b->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
-        b->chunk = kChunk;
-    }
-    int64_t left = nsteps;
-    while (b->exec && left >= b->chunk) {
-        TEUK_CUDA(cudaGraphLaunch(b->exec, b->stream));
-        left -= b->chunk;
-    }
-    for (; left > 0; --left) TEUK_CUDA(batch_launch_step(b));
-    for (int k = 0; k < b->n; ++k) b->t[k] += (double)nsteps * b->dt[k];
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_batch_step", [&]() -> teuk_status {
+        NvtxRange trace("teuk_batch_step");
+        if (!b) return fail(TEUK_ERR_ARG, "batch is NULL");
+        if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+        const int kChunk = 16;
+        if (nsteps >= kChunk && !b->exec) {
+            cudaGraph_t g = nullptr;
+            TEUK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < kChunk && e == cudaSuccess; ++k) e = batch_launch_step(b);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                b->exec = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+            b->chunk = kChunk;
+        }
+        int64_t left = nsteps;
+        while (b->exec && left >= b->chunk) {
+            TEUK_CUDA(cudaGraphLaunch(b->exec, b->stream));
+            left -= b->chunk;
+        }
+        for (; left > 0; --left) TEUK_CUDA(batch_launch_step(b));
+        for (int k = 0; k < b->n; ++k) b->t[k] += (double)nsteps * b->dt[k];
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_batch_get_info(const teuk_batch* b, int k, double* dt_out, double* t_out,
                                 int* seg_out, int* ctas_per_sm_out) {
-    if (!b || k < 0 || k >= b->n) return fail(TEUK_ERR_ARG, "bad argument");
-    if (dt_out) *dt_out = b->dt[k];
-    if (t_out) *t_out = b->t[k];
-    if (seg_out) *seg_out = b->seg;
-    if (ctas_per_sm_out) *ctas_per_sm_out = b->ctas;
-    return TEUK_OK;
+    return guarded("teuk_batch_get_info", [&]() -> teuk_status {
+        if (!b || k < 0 || k >= b->n) return fail(TEUK_ERR_ARG, "bad argument");
+        if (dt_out) *dt_out = b->dt[k];
+        if (t_out) *t_out = b->t[k];
+        if (seg_out) *seg_out = b->seg;
+        if (ctas_per_sm_out) *ctas_per_sm_out = b->ctas;
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_destroy(teuk_handle* h) {
@@ -476,231 +503,262 @@ teuk_status teuk_destroy(teuk_handle* h) {
 }
 
 teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
-    NvtxRange trace("teuk_create");
-    if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    teuk_status st = teuk_check_params(p);
-    if (st != TEUK_OK) return st;
-    teuk_handle* h = new teuk_handle();
-    h->p = *p;
-    st = teuk_stable_dt(p, &h->dt);
-    if (st != TEUK_OK) { delete h; return st; }
-    const size_t n = h->plane();
-    std::vector<double> coef((size_t)coef_planes(*p) * n);
-    st = teuk_build_coefficients(p, h->dt, coef.data());
-    if (st != TEUK_OK) { delete h; return st; }
-    cudaError_t e = cudaSuccess;
-    if (stream) {
-        h->stream = (cudaStream_t)stream;
-    } else {
-        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        h->own_stream = (e == cudaSuccess);
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&h->u, 4 * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->w, 4 * scratch_states(*p) * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->coef, coef.size() * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->obs, 8 * (size_t)p->ntheta * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 4 * n * sizeof(double), h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->coef, coef.data(), coef.size() * sizeof(double),
-                            cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-        teuk_destroy(h);
-        return cuda_fail(e, "teuk_create");
-    }
-    *out = h;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_create", [&]() -> teuk_status {
+        NvtxRange trace("teuk_create");
+        if (!out) return fail(TEUK_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        teuk_status st = teuk_check_params(p);
+        if (st != TEUK_OK) return st;
+        double dt = 0.0;
+        st = teuk_stable_dt(p, &dt);
+        if (st != TEUK_OK) return st;
+        const size_t n = (size_t)p->nr * p->ntheta;
+        std::vector<double> coef((size_t)coef_planes(*p) * n);       // may throw: nothing held yet
+        st = teuk_build_coefficients(p, dt, coef.data());
+        if (st != TEUK_OK) return st;
+        teuk_handle* h = new teuk_handle();
+        h->p = *p;
+        h->dt = dt;
+        cudaError_t e = cudaSuccess;
+        if (stream) {
+            h->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            h->own_stream = (e == cudaSuccess);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&h->u, 4 * n * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->w, 4 * scratch_states(*p) * n * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->coef, coef.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->obs, 8 * (size_t)p->ntheta * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 4 * n * sizeof(double), h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->coef, coef.data(), coef.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            teuk_destroy(h);
+            return cuda_fail(e, "teuk_create");
+        }
+        *out = h;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_get_info(const teuk_handle* h, teuk_params* p_out, double* dt_out,
                           double* t_out) {
-    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
-    if (p_out) *p_out = h->p;
-    if (dt_out) *dt_out = h->dt;
-    if (t_out) *t_out = h->t;
-    return TEUK_OK;
+    return guarded("teuk_get_info", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (p_out) *p_out = h->p;
+        if (dt_out) *dt_out = h->dt;
+        if (t_out) *t_out = h->t;
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_set_state(teuk_handle* h, const double* u_host, double t) {
-    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
-    TEUK_CUDA(cudaMemcpyAsync(h->u, u_host, 4 * h->plane() * sizeof(double),
-                              cudaMemcpyHostToDevice, h->stream));
-    TEUK_CUDA(cudaStreamSynchronize(h->stream));
-    h->t = t;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_set_state", [&]() -> teuk_status {
+        if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+        TEUK_CUDA(cudaMemcpyAsync(h->u, u_host, 4 * h->plane() * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream));
+        TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        h->t = t;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out) {
-    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
-    TEUK_CUDA(cudaMemcpyAsync(u_host, h->u, 4 * h->plane() * sizeof(double),
-                              cudaMemcpyDeviceToHost, h->stream));
-    TEUK_CUDA(cudaStreamSynchronize(h->stream));
-    if (t_out) *t_out = h->t;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_get_state", [&]() -> teuk_status {
+        if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+        TEUK_CUDA(cudaMemcpyAsync(u_host, h->u, 4 * h->plane() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        if (t_out) *t_out = h->t;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_set_state_async(teuk_handle* h, const double* u_host, double t) {
-    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
-    TEUK_CUDA(cudaMemcpyAsync(h->u, u_host, 4 * h->plane() * sizeof(double),
-                              cudaMemcpyHostToDevice, h->stream));
-    h->t = t;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_set_state_async", [&]() -> teuk_status {
+        if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+        TEUK_CUDA(cudaMemcpyAsync(h->u, u_host, 4 * h->plane() * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream));
+        h->t = t;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_get_state_async(teuk_handle* h, double* u_host) {
-    if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
-    TEUK_CUDA(cudaMemcpyAsync(u_host, h->u, 4 * h->plane() * sizeof(double),
-                              cudaMemcpyDeviceToHost, h->stream));
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_get_state_async", [&]() -> teuk_status {
+        if (!h || !u_host) return fail(TEUK_ERR_ARG, "NULL argument");
+        TEUK_CUDA(cudaMemcpyAsync(u_host, h->u, 4 * h->plane() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_synchronize(teuk_handle* h) {
-    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
-    TEUK_CUDA(cudaStreamSynchronize(h->stream));
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_synchronize", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_set_initial(teuk_handle* h, const double* psi, const double* pi) {
-    if (!h || !psi || !pi) return fail(TEUK_ERR_ARG, "NULL argument");
-    const size_t n = h->plane();
-    std::vector<double> u(4 * n);
-    for (size_t k = 0; k < n; ++k) {
-        u[k] = psi[2 * k];
-        u[n + k] = psi[2 * k + 1];
-        u[2 * n + k] = pi[2 * k];
-        u[3 * n + k] = pi[2 * k + 1];
-    }
-    return teuk_set_state(h, u.data(), 0.0);
+    return guarded("teuk_set_initial", [&]() -> teuk_status {
+        if (!h || !psi || !pi) return fail(TEUK_ERR_ARG, "NULL argument");
+        const size_t n = h->plane();
+        std::vector<double> u(4 * n);
+        for (size_t k = 0; k < n; ++k) {
+            u[k] = psi[2 * k];
+            u[n + k] = psi[2 * k + 1];
+            u[2 * n + k] = pi[2 * k];
+            u[3 * n + k] = pi[2 * k + 1];
+        }
+        return teuk_set_state(h, u.data(), 0.0);
+    });
 }
 
 teuk_status teuk_set_gaussian(teuk_handle* h, double rc, double width, const double* coeffs,
                               int nl, uint64_t seed) {
-    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
-    if (nl < 1 || nl > 16) return fail(TEUK_ERR_ARG, "nl must be in 1..16");
-    if (!(width > 0.0) || !std::isfinite(width) || !std::isfinite(rc))
-        return fail(TEUK_ERR_ARG, "need finite rc and width > 0");
-    const teuk_params& p = h->p;
-    const int nr = p.nr, nth = p.ntheta;
-    const size_t n = h->plane();
-    std::vector<double> cre(nl), cim(nl);
-    uint64_t state = seed;
-    for (int k = 0; k < nl; ++k) {
-        if (coeffs) {
-            cre[k] = coeffs[2 * k];
-            cim[k] = coeffs[2 * k + 1];
-        } else {
-            const double amp = 0.5 + (double)(splitmix64(state) >> 11) * 0x1.0p-53;
-            const double ph = 2.0 * M_PI * (double)(splitmix64(state) >> 11) * 0x1.0p-53;
-            cre[k] = amp * std::cos(ph);
-            cim[k] = amp * std::sin(ph);
-        }
-    }
-    const int l0 = std::max(std::abs(p.s), std::abs(p.m));
-    const double hs = (p.rstar_max - p.rstar_min) / (nr - 1);
-    std::vector<double> radial(nr), ang((size_t)nl * nth);
-    for (int i = 0; i < nr; ++i) {
-        const double z = (p.rstar_min + i * hs - rc) / width;
-        radial[i] = std::exp(-0.5 * z * z);
-    }
-    for (int k = 0; k < nl; ++k)
-        for (int j = 0; j < nth; ++j)
-            ang[(size_t)k * nth + j] = swsh(p.s, l0 + k, p.m, (j + 0.5) * M_PI / nth);
-    std::vector<double> u(4 * n, 0.0);
-    for (int j = 0; j < nth; ++j) {
-        double are = 0.0, aim = 0.0;
+    return guarded("teuk_set_gaussian", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (nl < 1 || nl > 16) return fail(TEUK_ERR_ARG, "nl must be in 1..16");
+        if (!(width > 0.0) || !std::isfinite(width) || !std::isfinite(rc))
+            return fail(TEUK_ERR_ARG, "need finite rc and width > 0");
+        const teuk_params& p = h->p;
+        const int nr = p.nr, nth = p.ntheta;
+        const size_t n = h->plane();
+        std::vector<double> cre(nl), cim(nl);
+        uint64_t state = seed;
         for (int k = 0; k < nl; ++k) {
-            are += cre[k] * ang[(size_t)k * nth + j];
-            aim += cim[k] * ang[(size_t)k * nth + j];
+            if (coeffs) {
+                cre[k] = coeffs[2 * k];
+                cim[k] = coeffs[2 * k + 1];
+            } else {
+                const double amp = 0.5 + (double)(splitmix64(state) >> 11) * 0x1.0p-53;
+                const double ph = 2.0 * M_PI * (double)(splitmix64(state) >> 11) * 0x1.0p-53;
+                cre[k] = amp * std::cos(ph);
+                cim[k] = amp * std::sin(ph);
+            }
         }
+        const int l0 = std::max(std::abs(p.s), std::abs(p.m));
+        const double hs = (p.rstar_max - p.rstar_min) / (nr - 1);
+        std::vector<double> radial(nr), ang((size_t)nl * nth);
         for (int i = 0; i < nr; ++i) {
-            u[(size_t)j * nr + i] = are * radial[i];
-            u[n + (size_t)j * nr + i] = aim * radial[i];
+            const double z = (p.rstar_min + i * hs - rc) / width;
+            radial[i] = std::exp(-0.5 * z * z);
         }
-    }
-    return teuk_set_state(h, u.data(), 0.0);
+        for (int k = 0; k < nl; ++k)
+            for (int j = 0; j < nth; ++j)
+                ang[(size_t)k * nth + j] = swsh(p.s, l0 + k, p.m, (j + 0.5) * M_PI / nth);
+        std::vector<double> u(4 * n, 0.0);
+        for (int j = 0; j < nth; ++j) {
+            double are = 0.0, aim = 0.0;
+            for (int k = 0; k < nl; ++k) {
+                are += cre[k] * ang[(size_t)k * nth + j];
+                aim += cim[k] * ang[(size_t)k * nth + j];
+            }
+            for (int i = 0; i < nr; ++i) {
+                u[(size_t)j * nr + i] = are * radial[i];
+                u[n + (size_t)j * nr + i] = aim * radial[i];
+            }
+        }
+        return teuk_set_state(h, u.data(), 0.0);
+    });
 }
 
 teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
-    NvtxRange trace("teuk_step");
-    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
-    if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
-    const int kChunk = 16;
-    if (nsteps >= kChunk && !h->exec) {
-        cudaGraph_t g = nullptr;
-        TEUK_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k < kChunk && e == cudaSuccess; ++k)
-            e = launch_step(h->p, h->coef, h->dt, h->u, h->w, h->stream);
-        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
-        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&h->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) { h->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
-        h->chunk = kChunk;
-    }
-    int64_t left = nsteps;
-    while (h->exec && left >= h->chunk) {
-        TEUK_CUDA(cudaGraphLaunch(h->exec, h->stream));
-        left -= h->chunk;
-    }
-    for (; left > 0; --left)
-        TEUK_CUDA(launch_step(h->p, h->coef, h->dt, h->u, h->w, h->stream));
-    h->t += (double)nsteps * h->dt;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_step", [&]() -> teuk_status {
+        NvtxRange trace("teuk_step");
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+        const int kChunk = 16;
+        if (nsteps >= kChunk && !h->exec) {
+            cudaGraph_t g = nullptr;
+            TEUK_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < kChunk && e == cudaSuccess; ++k)
+                e = launch_step(h->p, h->coef, h->dt, h->u, h->w, h->stream);
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+            if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture"); }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&h->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                h->exec = nullptr;
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+            h->chunk = kChunk;
+        }
+        int64_t left = nsteps;
+        while (h->exec && left >= h->chunk) {
+            TEUK_CUDA(cudaGraphLaunch(h->exec, h->stream));
+            left -= h->chunk;
+        }
+        for (; left > 0; --left)
+            TEUK_CUDA(launch_step(h->p, h->coef, h->dt, h->u, h->w, h->stream));
+        h->t += (double)nsteps * h->dt;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_observe(teuk_handle* h, double rstar_ext, double* wave, double* horizon,
                          double* t_out) {
-    NvtxRange trace("teuk_observe");
-    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
-    if (!std::isfinite(rstar_ext)) return fail(TEUK_ERR_ARG, "rstar_ext not finite");
-    const int nr = h->p.nr, nth = h->p.ntheta;
-    const double hstep = (h->p.rstar_max - h->p.rstar_min) / (nr - 1);
-    long ie = std::lround((rstar_ext - h->p.rstar_min) / hstep);
-    ie = ie < 0 ? 0 : (ie > nr - 1 ? nr - 1 : ie);
-    observe_kernel<<<(nth + 127) / 128, 128, 0, h->stream>>>(
-        h->u, nr, nth, (long long)h->plane(), (int)ie, 0.5 / hstep, h->obs);
-    TEUK_CUDA(cudaGetLastError());
-    std::vector<double> o(8 * (size_t)nth);
-    TEUK_CUDA(cudaMemcpyAsync(o.data(), h->obs, o.size() * sizeof(double),
-                              cudaMemcpyDeviceToHost, h->stream));
-    TEUK_CUDA(cudaStreamSynchronize(h->stream));
-    for (double v : o)
-        if (!std::isfinite(v)) return fail(TEUK_ERR_NONFINITE, "observed value is not finite");
-    if (wave) std::memcpy(wave, o.data(), 2 * (size_t)nth * sizeof(double));
-    if (horizon) std::memcpy(horizon, o.data() + 2 * nth, 6 * (size_t)nth * sizeof(double));
-    if (t_out) *t_out = h->t;
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_observe", [&]() -> teuk_status {
+        NvtxRange trace("teuk_observe");
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (!std::isfinite(rstar_ext)) return fail(TEUK_ERR_ARG, "rstar_ext not finite");
+        const int nr = h->p.nr, nth = h->p.ntheta;
+        const double hstep = (h->p.rstar_max - h->p.rstar_min) / (nr - 1);
+        long ie = std::lround((rstar_ext - h->p.rstar_min) / hstep);
+        ie = ie < 0 ? 0 : (ie > nr - 1 ? nr - 1 : ie);
+        observe_kernel<<<(nth + 127) / 128, 128, 0, h->stream>>>(
+            h->u, nr, nth, (long long)h->plane(), (int)ie, 0.5 / hstep, h->obs);
+        TEUK_CUDA(cudaGetLastError());
+        std::vector<double> o(8 * (size_t)nth);
+        TEUK_CUDA(cudaMemcpyAsync(o.data(), h->obs, o.size() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        for (double v : o)
+            if (!std::isfinite(v)) return fail(TEUK_ERR_NONFINITE, "observed value is not finite");
+        if (wave) std::memcpy(wave, o.data(), 2 * (size_t)nth * sizeof(double));
+        if (horizon) std::memcpy(horizon, o.data() + 2 * nth, 6 * (size_t)nth * sizeof(double));
+        if (t_out) *t_out = h->t;
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_check_finite(teuk_handle* h) {
-    if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
-    TEUK_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
-    nonfinite_kernel<<<304, 256, 0, h->stream>>>(h->u, 4 * (long long)h->plane(), h->flag);
-    TEUK_CUDA(cudaGetLastError());
-    int flag = 0;
-    TEUK_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    TEUK_CUDA(cudaStreamSynchronize(h->stream));
-    if (flag) return fail(TEUK_ERR_NONFINITE, "state holds NaN or infinity");
-    clear_error();
-    return TEUK_OK;
+    return guarded("teuk_check_finite", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        TEUK_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+        nonfinite_kernel<<<304, 256, 0, h->stream>>>(h->u, 4 * (long long)h->plane(), h->flag);
+        TEUK_CUDA(cudaGetLastError());
+        int flag = 0;
+        TEUK_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        if (flag) return fail(TEUK_ERR_NONFINITE, "state holds NaN or infinity");
+        clear_error();
+        return TEUK_OK;
+    });
 }
 
 teuk_status teuk_state_dev(teuk_handle* h, double** u_dev) {
-    if (!h || !u_dev) return fail(TEUK_ERR_ARG, "NULL argument");
-    *u_dev = h->u;
-    return TEUK_OK;
+    return guarded("teuk_state_dev", [&]() -> teuk_status {
+        if (!h || !u_dev) return fail(TEUK_ERR_ARG, "NULL argument");
+        *u_dev = h->u;
+        return TEUK_OK;
+    });
 }
 
 }  // extern "C"

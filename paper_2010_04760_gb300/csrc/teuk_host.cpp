@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -18,6 +19,15 @@ teuk_status fail(teuk_status st, const std::string& msg) {
     return st;
 }
 void clear_error() { g_last_error.clear(); }
+
+teuk_status fail_host(const char* what, const char* why) noexcept {
+    try {
+        g_last_error = std::string(what) + ": " + why;
+    } catch (...) {
+        g_last_error.clear();     // clear() never allocates
+    }
+    return TEUK_ERR_HOST;
+}
 
 // Tortoise coordinate (Sec. 2.2): dr*/dr = (r^2+a^2)/Delta. The unknown is
 // y = ln(r - r_+), so the horizon region (r* -> -infinity) stays resolved and
@@ -254,9 +264,16 @@ static void for_rows(int nth, long long work, F body) {
     if (work < (1LL << 16)) nt = 1;
     nt = std::min<unsigned>(nt, (unsigned)nth);
     std::vector<std::thread> pool;
+    pool.reserve(nt);
     for (unsigned t = 0; t < nt; ++t) {
         const int j0 = (int)((long long)nth * t / nt), j1 = (int)((long long)nth * (t + 1) / nt);
-        pool.emplace_back(body, j0, j1);
+        bool started = false;
+        try {
+            pool.emplace_back(body, j0, j1);
+            started = true;
+        } catch (const std::system_error&) {
+        }
+        if (!started) body(j0, j1);     // no thread available: this range here
     }
     for (auto& th : pool) th.join();
 }
@@ -275,6 +292,7 @@ const char* teuk_status_str(teuk_status st) {
     case TEUK_ERR_NONFINITE: return "non-finite state";
     case TEUK_ERR_TIMEOUT: return "device wait timed out";
     case TEUK_ERR_STATE: return "call out of order";
+    case TEUK_ERR_HOST: return "host resource unavailable";
     }
     return "unknown status";
 }
@@ -329,34 +347,36 @@ teuk_status teuk_check_params(const teuk_params* p) {
 }
 
 teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
-    teuk_status st = teuk_check_params(p);
-    if (st != TEUK_OK) return st;
-    if (!dt_out) return fail(TEUK_ERR_ARG, "dt_out is NULL");
-    if (p->dt > 0.0) { *dt_out = p->dt; return TEUK_OK; }
-    const double h = (p->rstar_max - p->rstar_min) / (p->nr - 1);
-    const double dth = M_PI / p->ntheta;
-    std::vector<double> r, x;
-    radial_nodes(*p, r, x);
-    std::vector<double> row_lam(p->ntheta, 0.0);
-    for_rows(p->ntheta, (long long)p->nr * p->ntheta, [&](int j0, int j1) {
-        for (int j = j0; j < j1; ++j) {
-            double lam = 0.0;
-            for (int i = 0; i < p->nr; ++i) {
-                PointCoef c = node_coefficients(r[i], x[i], (j + 0.5) * dth, *p);
-                double kappa = c.Ath * (16.0 / 3.0) / (dth * dth) + std::fabs(c.Bth) * 1.5 / dth +
-                               std::hypot(c.Cr, c.Ci);
-                const double speed = std::fmax(std::fabs(c.b), std::fabs(c.c));
-                lam = std::fmax(lam, speed / h + std::sqrt(kappa));
+    return guarded("teuk_stable_dt", [&]() -> teuk_status {
+        teuk_status st = teuk_check_params(p);
+        if (st != TEUK_OK) return st;
+        if (!dt_out) return fail(TEUK_ERR_ARG, "dt_out is NULL");
+        if (p->dt > 0.0) { *dt_out = p->dt; return TEUK_OK; }
+        const double h = (p->rstar_max - p->rstar_min) / (p->nr - 1);
+        const double dth = M_PI / p->ntheta;
+        std::vector<double> r, x;
+        radial_nodes(*p, r, x);
+        std::vector<double> row_lam(p->ntheta, 0.0);
+        for_rows(p->ntheta, (long long)p->nr * p->ntheta, [&](int j0, int j1) {
+            for (int j = j0; j < j1; ++j) {
+                double lam = 0.0;
+                for (int i = 0; i < p->nr; ++i) {
+                    PointCoef c = node_coefficients(r[i], x[i], (j + 0.5) * dth, *p);
+                    double kappa = c.Ath * (16.0 / 3.0) / (dth * dth) +
+                                   std::fabs(c.Bth) * 1.5 / dth + std::hypot(c.Cr, c.Ci);
+                    const double speed = std::fmax(std::fabs(c.b), std::fabs(c.c));
+                    lam = std::fmax(lam, speed / h + std::sqrt(kappa));
+                }
+                row_lam[j] = lam;
             }
-            row_lam[j] = lam;
-        }
+        });
+        double lam = 0.0;
+        for (double v : row_lam) lam = std::fmax(lam, v);
+        // SSP-RK(10,4): 2.8 = min(4.92 / sqrt(3), 13.9 / 2.51), its imaginary- and
+        // real-axis stability extents relative to SSP-RK(3,3)
+        *dt_out = (p->rk == TEUK_RK_SSP104 ? 2.8 : 1.0) * p->cfl / lam;
+        return TEUK_OK;
     });
-    double lam = 0.0;
-    for (double v : row_lam) lam = std::fmax(lam, v);
-    // SSP-RK(10,4): 2.8 = min(4.92 / sqrt(3), 13.9 / 2.51), its imaginary- and
-    // real-axis stability extents relative to SSP-RK(3,3)
-    *dt_out = (p->rk == TEUK_RK_SSP104 ? 2.8 : 1.0) * p->cfl / lam;
-    return TEUK_OK;
 }
 
 size_t teuk_coeff_count(const teuk_params* p) {
@@ -365,58 +385,60 @@ size_t teuk_coeff_count(const teuk_params* p) {
 }
 
 teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coef) {
-    teuk_status st = teuk_check_params(p);
-    if (st != TEUK_OK) return st;
-    if (!coef) return fail(TEUK_ERR_ARG, "coef_host is NULL");
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
-    const int nr = p->nr, nth = p->ntheta;
-    const size_t plane = (size_t)nr * nth;
-    const double h = (p->rstar_max - p->rstar_min) / (nr - 1);
-    const double dth = M_PI / nth;
-    const double sigma = ((p->m + p->s) % 2 == 0) ? 1.0 : -1.0;   // pole parity
-    dt = stage_step(*p, dt);                 // forward-Euler step of one stage
-    const double c6h = dt / (6.0 * h);
-    std::vector<double> r, x;
-    radial_nodes(*p, r, x);
-    for_rows(nth, (long long)nr * nth, [&](int j0, int j1) {
-    for (int j = j0; j < j1; ++j) {
-        const double th = (j + 0.5) * dth;
-        for (int i = 0; i < nr; ++i) {
-            PointCoef c = node_coefficients(r[i], x[i], th, *p);
-            const size_t q = (size_t)j * nr + i;
-            coef[kCb * plane + q] = c6h * c.b;
-            if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) coef[kCc * plane + q] = c6h * c.c;
-            coef[kCKr * plane + q] = c6h * c.Kr;
-            coef[kCKi * plane + q] = c6h * c.Ki;
-            coef[kCBr * plane + q] = dt * c.Btr;
-            coef[kCBi * plane + q] = dt * c.Bti;
-            coef[kCCi * plane + q] = dt * c.Ci;
-            // fourth-order centred theta differences:
-            //   12 dth^2 Psi_thth = -P(j+2) + 16 P(j+1) - 30 P(j) + 16 P(j-1) - P(j-2)
-            //   12 dth   Psi_th   = -P(j+2) +  8 P(j+1)            -  8 P(j-1) + P(j-2)
-            const bool weno_th = p->theta_mode == TEUK_THETA_WENO5;
-            const double A = dt * c.Ath / (12.0 * dth * dth);
-            const double B = weno_th ? 0.0 : dt * c.Bth / (12.0 * dth);
-            if (weno_th) coef[kCBth * plane + q] = dt * c.Bth / (6.0 * dth);
-            else if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) coef[kCBth * plane + q] = 0.0;
-            double w[5] = {-A + B, 16.0 * A - 8.0 * B, -30.0 * A + dt * c.Cr,
-                           16.0 * A + 8.0 * B, -A - B};
-            // Rows outside [0, nth) mirror across the pole with parity sigma:
-            // row -1 -> 0, -2 -> 1, nth -> nth-1, nth+1 -> nth-2.
-            for (int k = -2; k <= 2; ++k) {
-                const int jj = j + k;
-                int tgt;
-                if (jj < 0) tgt = -1 - jj;
-                else if (jj >= nth) tgt = 2 * nth - 1 - jj;
-                else continue;
-                w[tgt - j + 2] += sigma * w[k + 2];
-                w[k + 2] = 0.0;
+    return guarded("teuk_build_coefficients", [&]() -> teuk_status {
+        teuk_status st = teuk_check_params(p);
+        if (st != TEUK_OK) return st;
+        if (!coef) return fail(TEUK_ERR_ARG, "coef_host is NULL");
+        if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
+        const int nr = p->nr, nth = p->ntheta;
+        const size_t plane = (size_t)nr * nth;
+        const double h = (p->rstar_max - p->rstar_min) / (nr - 1);
+        const double dth = M_PI / nth;
+        const double sigma = ((p->m + p->s) % 2 == 0) ? 1.0 : -1.0;   // pole parity
+        dt = stage_step(*p, dt);                 // forward-Euler step of one stage
+        const double c6h = dt / (6.0 * h);
+        std::vector<double> r, x;
+        radial_nodes(*p, r, x);
+        for_rows(nth, (long long)nr * nth, [&](int j0, int j1) {
+        for (int j = j0; j < j1; ++j) {
+            const double th = (j + 0.5) * dth;
+            for (int i = 0; i < nr; ++i) {
+                PointCoef c = node_coefficients(r[i], x[i], th, *p);
+                const size_t q = (size_t)j * nr + i;
+                coef[kCb * plane + q] = c6h * c.b;
+                if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) coef[kCc * plane + q] = c6h * c.c;
+                coef[kCKr * plane + q] = c6h * c.Kr;
+                coef[kCKi * plane + q] = c6h * c.Ki;
+                coef[kCBr * plane + q] = dt * c.Btr;
+                coef[kCBi * plane + q] = dt * c.Bti;
+                coef[kCCi * plane + q] = dt * c.Ci;
+                // fourth-order centred theta differences:
+                //   12 dth^2 Psi_thth = -P(j+2) + 16 P(j+1) - 30 P(j) + 16 P(j-1) - P(j-2)
+                //   12 dth   Psi_th   = -P(j+2) +  8 P(j+1)            -  8 P(j-1) + P(j-2)
+                const bool weno_th = p->theta_mode == TEUK_THETA_WENO5;
+                const double A = dt * c.Ath / (12.0 * dth * dth);
+                const double B = weno_th ? 0.0 : dt * c.Bth / (12.0 * dth);
+                if (weno_th) coef[kCBth * plane + q] = dt * c.Bth / (6.0 * dth);
+                else if (p->coords == TEUK_COORDS_HYPERBOLOIDAL) coef[kCBth * plane + q] = 0.0;
+                double w[5] = {-A + B, 16.0 * A - 8.0 * B, -30.0 * A + dt * c.Cr,
+                               16.0 * A + 8.0 * B, -A - B};
+                // Rows outside [0, nth) mirror across the pole with parity sigma:
+                // row -1 -> 0, -2 -> 1, nth -> nth-1, nth+1 -> nth-2.
+                for (int k = -2; k <= 2; ++k) {
+                    const int jj = j + k;
+                    int tgt;
+                    if (jj < 0) tgt = -1 - jj;
+                    else if (jj >= nth) tgt = 2 * nth - 1 - jj;
+                    else continue;
+                    w[tgt - j + 2] += sigma * w[k + 2];
+                    w[k + 2] = 0.0;
+                }
+                for (int k = 0; k < 5; ++k) coef[(kWm2 + k) * plane + q] = w[k];
             }
-            for (int k = 0; k < 5; ++k) coef[(kWm2 + k) * plane + q] = w[k];
         }
-    }
+        });
+        return TEUK_OK;
     });
-    return TEUK_OK;
 }
 
 }  // extern "C"

@@ -2,6 +2,8 @@
 // the library. Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include "../../include/teuk.h"
 
@@ -35,6 +37,24 @@ inline double stage_step(const teuk_params& p, double dt) {
 
 teuk_status fail(teuk_status st, const std::string& msg);
 void clear_error();
+// TEUK_ERR_HOST with "what: why"; allocates nothing that can throw out of it.
+teuk_status fail_host(const char* what, const char* why) noexcept;
+
+// Runs body() (returning teuk_status) and turns a C++ exception escaping it
+// (a failed host allocation, a thread that could not start) into
+// TEUK_ERR_HOST, so that no exception crosses the C ABI.
+template <class F>
+teuk_status guarded(const char* what, F&& body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return fail_host(what, "host memory exhausted");
+    } catch (const std::exception& ex) {
+        return fail_host(what, ex.what());
+    } catch (...) {
+        return fail_host(what, "unknown host exception");
+    }
+}
 
 // r(r*) and the continuum coefficients at one node, real arithmetic.
 struct PointCoef {

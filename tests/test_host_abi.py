@@ -27,8 +27,9 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_status_strings():
-    for st in range(6):
-        assert T.teuk_status_str(st)
+    names = [T.teuk_status_str(st) for st in range(7)]
+    assert all(names) and len(set(names)) == 7
+    assert T.teuk_status_str(7) == "unknown status"
 
 
 @pytest.mark.parametrize("field,value", [("nr", 6), ("ntheta", 4), ("a", 1.5), ("M", 0.0),
@@ -264,3 +265,39 @@ def test_plain_c_client_of_the_abi(tmp_path):
     assert float(got["coef_abs_sum"]) == pytest.approx(np.abs(T.teuk_build_coefficients(p, dt)).sum(),
                                                        rel=1e-12)   # summation order
     assert int(got["bad_status"]) == T.TEUK_ERR_ARG and got["bad_message_nonempty"] == "1"
+
+
+_HOST_OOM_CHILD = r"""
+import ctypes, resource, sys
+sys.path.insert(0, sys.argv[1])
+import paper_2010_04760_gb300 as T
+L = T.lib()
+limit = 2 << 30                                   # 2 GiB of address space from here on
+soft, hard = resource.getrlimit(resource.RLIMIT_AS)
+used = int(open("/proc/self/statm").read().split()[0]) * resource.getpagesize()
+resource.setrlimit(resource.RLIMIT_AS, (used + limit, hard))
+# 4e8 nodes with a given dt: the coefficient array alone would take 35 GB
+p = T.make_params(20000, 20000, dt=0.01)
+h = ctypes.c_void_p(12345)
+st = L.teuk_create(ctypes.byref(p), None, ctypes.byref(h))
+print(st, h.value, L.teuk_last_error().decode())
+"""
+
+
+def test_host_allocation_failure_is_a_status():
+    """A host allocation that fails inside a call comes back as
+    TEUK_ERR_HOST with a message and a NULL handle; no C++ exception crosses
+    the ABI (which would abort the process). The child process caps its
+    address space so that the coefficient array of a 4e8-node grid cannot be
+    allocated; nothing touches a GPU before that point."""
+    import subprocess
+    import sys
+    T.lib()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _HOST_OOM_CHILD, root], capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    st, handle, msg = out.stdout.strip().split(None, 2)
+    assert int(st) == T.TEUK_ERR_HOST
+    assert handle == "None"
+    assert msg == "teuk_create: host memory exhausted"
