@@ -26,14 +26,16 @@ _lib = None
 WPREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "f64r": 4}
 
 
-def build(force=False):
-    """Compile the oracle with gcc (plain -O2, no FMA contraction, OpenMP)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+def build(force=False, src=_SRC, out=_LIB):
+    """Compile the oracle with gcc (plain -O2, no FMA contraction, OpenMP).
+    ``src``/``out`` default to this package's source and library; the
+    mutation tests compile altered copies of the source to other paths."""
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-o", _LIB, _SRC, "-lm"]
+           "-I", _HERE, "-o", out, src, "-lm"]
     subprocess.check_call(cmd)
-    return _LIB
+    return out
 
 
 class Grid(ctypes.Structure):
@@ -50,8 +52,10 @@ class Grid(ctypes.Structure):
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        # TEUK_ORACLE_LIB names a prebuilt oracle library to load instead (the
+        # mutation tests run the pins against copies with planted mistakes)
+        path = os.environ.get("TEUK_ORACLE_LIB") or build()
+        lib = ctypes.CDLL(path)
         D, I, L, P = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
         sig = {
             "orc_rstar_of_r": (D, [D, D, D]),

@@ -162,6 +162,33 @@ def test_theta_weno_option_on_spin_weighted_harmonics(case, a):
     assert errs[-1] < 1e-5 * abs(lam) + 1e-9
 
 
+def test_theta_weno_stencil_lies_upwind():
+    """theta_mode 1 upwinds the Bth dPsi/dtheta term by the sign of its speed
+    -Bth (reading): Bth = Delta cot(theta)/Sigma^2 is positive in the
+    northern hemisphere, so there the derivative at row j uses the
+    negative-direction stencils (rows j-2 .. j+3) and row j-3 cannot enter
+    F_pi(j); in the southern hemisphere it is the mirror image (rows
+    j-3 .. j+2, row j+3 cannot enter). Rows j +- 3 enter only through this
+    derivative (the centred second difference spans j +- 2)."""
+    nr, nth = 12, 24
+    g = o.grid(nr, nth, -10.0, 10.0, 1.0, 0.6, 0, 0, 1e-6, "fp64", 1)
+    co = o.coefficients(g)
+    th = I.theta_nodes(nth)
+    rng = np.random.default_rng(5)
+    u = np.zeros((4, nth, nr))
+    u[0] = np.cos(th)[:, None] * (1.0 + 0.1 * rng.standard_normal(nr))[None, :]
+    u[1] = np.sin(2 * th)[:, None] * 0.5
+    F = o.rhs(g, co, u)
+    for j, quiet, loud in [(6, 3, 9), (nth - 1 - 6, nth - 1 - 3, nth - 1 - 9)]:
+        assert (co[8][j] > 0).all() == (j < nth // 2)
+        for row, moves in [(quiet, False), (loud, True)]:
+            v = u.copy()
+            v[0][row] += 0.3
+            v[1][row] -= 0.2
+            dF = np.abs(o.rhs(g, co, v)[2:4, j] - F[2:4, j])
+            assert (dF.max() > 1e-6) == moves, (j, row, dF.max())
+
+
 @pytest.mark.parametrize("scheme,coords", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_assembly_matches_printed_real_matrices(scheme, coords):
     """F = -(M du/dx + L u + A u) with M, A, L exactly as printed in Sec. 2.3,
@@ -210,6 +237,29 @@ def test_assembly_matches_printed_real_matrices(scheme, coords):
         assert err < (1e-12 if row < 2 else 2e-4) * scale, (row, err, scale)
 
 
+def test_kreiss_oliger_term_damps_in_the_right_hand_side():
+    """Sec. 3.1.1 leaves the sign of Q = sigma h^7 D+^4 D-^4 / 256 in the
+    evolution open; the damping reading subtracts it. On the sawtooth
+    (-1)^i, D+ D- multiplies by -4/h^2, so Q = (sigma/h) u and the scheme's
+    right-hand side must change by exactly -(sigma/h) u (in every component,
+    away from the ghost-affected edges) when sigma is switched on."""
+    nr, nth, sigma = 40, 6, 0.3
+    x0, x1 = -20.0, 40.0
+    h = (x1 - x0) / (nr - 1)
+    saw = (-1.0) ** np.arange(nr)
+    for comp in range(4):
+        u = np.zeros((4, nth, nr))
+        u[comp] = saw[None, :]
+        F = {}
+        for sg in (0.0, sigma):
+            g = o.grid(nr, nth, x0, x1, 1.0, 0.0, 0, 0, scheme=1, ko_sigma=sg)
+            F[sg] = o.rhs(g, o.coefficients(g), u)
+        diff = (F[sigma] - F[0.0])[:, :, 5:nr - 5]
+        want = np.zeros_like(diff)
+        want[comp] = -(sigma / h) * saw[None, 5:nr - 5]
+        np.testing.assert_allclose(diff, want, rtol=0, atol=1e-9 * sigma / h)
+
+
 def test_constant_scalar_state_is_stationary():
     for a in (0.0, 0.9):
         g = o.grid(40, 12, -20.0, 40.0, 1.0, a, 0, 0)
@@ -228,6 +278,9 @@ def test_observe_gathers_nodes_and_one_sided_derivative():
         u[c] = (c + 1) * (rs ** 2)[None, :] + np.arange(6)[:, None]
     wave, hor = o.observe(g, u, 20.4)
     np.testing.assert_array_equal(wave[:, 0], u[0][:, 30])
+    np.testing.assert_array_equal(o.observe(g, u, 20.6)[0][:, 1], u[1][:, 31])   # nearest node
+    np.testing.assert_array_equal(o.observe(g, u, -30.0)[0][:, 0], u[0][:, 0])   # clamped
+    np.testing.assert_array_equal(o.observe(g, u, 99.0)[0][:, 0], u[0][:, 49])
     np.testing.assert_array_equal(hor[:, 2], u[2][:, 0])
     np.testing.assert_allclose(hor[:, 4], 2 * rs[0] * 1, rtol=1e-12)
     np.testing.assert_allclose(hor[:, 5], 2 * rs[0] * 2, rtol=1e-12)

@@ -205,6 +205,8 @@ def test_reduced_weights_within_rounding_of_fp64_weights(wprec, dir):
         f64 = lib.orc_weno5_flux(0, dir, o._ptr(f5), 1e-6, None, None, None)
         bound = np.sum(np.abs(wo - w64) * np.abs(qo - qo[1])) + 1e-13 * np.max(np.abs(f5))
         assert abs(fW - f64) <= bound, (f5, fW, f64, bound)
+        # the promoted weights sum to one in binary64 (Sec. 3.1.3)
+        assert abs((wo[0] + wo[1]) + wo[2] - 1.0) <= 2.0 ** -52, wo
     assert worst < 12.0, worst
 
 
