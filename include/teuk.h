@@ -31,7 +31,11 @@
  *    A failing call leaves its outputs unspecified and the handle usable
  *    unless the status is TEUK_ERR_CUDA.
  *  - "stream" arguments are cudaStream_t values passed as void* (NULL = the
- *    legacy default stream).
+ *    legacy default stream, except in teuk_create and teuk_batch_create,
+ *    where NULL gives the handle a non-blocking stream of its own).
+ *  - Host threads: calls on different handles (or batches) may run at the
+ *    same time on different threads; one handle must not be used by two
+ *    threads at once. teuk_last_error is per thread.
  */
 #ifndef TEUK_H
 #define TEUK_H
@@ -250,7 +254,8 @@ teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* 
 
 /* Allocate the state, stage buffers and coefficient array on the current
  * device and build the coefficients (teuk_stable_dt when p->dt == 0).
- * stream: the CUDA stream every later call of this handle runs on.
+ * stream: the CUDA stream every later call of this handle runs on; NULL
+ * creates a non-blocking stream that teuk_destroy destroys.
  * The state starts at zero, t = 0. */
 teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out);
 
