@@ -2,36 +2,54 @@
 
     python -m paper_2010_04760_gb300.throughput [--steps 20]
 
-For each workload and weight format: point-stage updates per second (nodes x 3
-stages per SSP-RK(3,3) step), device-timed with CUDA events around each step
-through a handle (one teuk_step call per step), L2 flushed before every step
-by writing a 256 MiB buffer, as the benchmark does; the HBM figure divides
-the algorithmic bytes of a point-stage (coefficient planes, u_prev, u_out and
-2/3 of u^n) by the time. Prints one table row per case.
+For each workload and weight format: point-stage updates per second (nodes x
+stages per step: 3 for SSP-RK(3,3), 10 for SSP-RK(10,4)), device-timed with
+CUDA events around each step through a handle (one teuk_step call per step),
+L2 flushed before every step by writing a 256 MiB buffer, as the benchmark
+does; the HBM figure divides the algorithmic bytes of a point-stage
+(coefficient planes, u_prev, u_out and, for SSP-RK(3,3), 2/3 of u^n) by the
+time, and "M/s" is simulated time (units of M) advanced per second. The last
+rows run the paper's comparison scheme (FD6 + KO8, Sec. 3.1.1) and its
+second integrator (SSP-RK(10,4), Sec. 3.2). Prints one table row per case.
 """
 import argparse
 
 import numpy as np
 
 from . import inputs as I
-from . import params_from_workload, teuk_create, teuk_set_state, teuk_step
+from . import (TEUK_RK_SSP104, TEUK_SCHEME_FD6_KO8, params_from_workload, teuk_create,
+               teuk_get_info, teuk_set_state, teuk_step)
 
+FD6 = {"scheme": TEUK_SCHEME_FD6_KO8}
+RK104 = {"rk": TEUK_RK_SSP104}
+# (workload, weight formats, parameter overrides, label)
 CASES = [
-    (I.SCHW_SCALAR, ("fp64", "fp32")),
-    (I.KERR_GRAV, ("fp64", "fp32", "fp16", "bf16")),
-    (I.EXTREMAL_SCALAR, ("fp64", "fp32", "fp16", "bf16")),
-    (I.TAIL_SCALAR, ("fp64", "fp32")),
-    (I.EXTREMAL_GRAV_HYP, ("fp64", "fp32", "fp16", "bf16")),
+    (I.SCHW_SCALAR, ("fp64", "fp32"), {}, ""),
+    (I.KERR_GRAV, ("fp64", "fp32", "fp16", "bf16"), {}, ""),
+    (I.EXTREMAL_SCALAR, ("fp64", "fp32", "fp16", "bf16"), {}, ""),
+    (I.TAIL_SCALAR, ("fp64", "fp32"), {}, ""),
+    (I.EXTREMAL_GRAV_HYP, ("fp64", "fp32", "fp16", "bf16"), {}, ""),
+    (I.KERR_GRAV, ("fp64",), FD6, " FD6+KO8"),
+    (I.EXTREMAL_GRAV_HYP, ("fp64",), FD6, " FD6+KO8"),
+    (I.KERR_GRAV, ("fp64", "fp32"), RK104, " RK(10,4)"),
+    (I.EXTREMAL_GRAV_HYP, ("fp64", "fp32"), RK104, " RK(10,4)"),
 ]
 
 
-def bytes_per_point_stage(wl):
+def bytes_per_point_stage(wl, rk104=False):
+    """Coefficients, u_prev, u_out, plus: SSP-RK(3,3) reads u^n in two of its
+    three stages; SSP-RK(10,4) reads q in its last stage and its combination
+    kernel reads two states and writes two (160 B per node per ten stages)."""
     planes = 12 if wl.coords == 1 else 11        # the kernel reads 12 of the 13 planes
-    return 8.0 * planes + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
+    return 8.0 * planes + 32.0 + 32.0 + (16.0 if rk104 else 32.0 * 2.0 / 3.0)
 
 
-def time_case(torch, wl, wprec, steps, stream, flush):
-    h = teuk_create(params_from_workload(wl, wprec=wprec), stream)
+def time_case(torch, wl, wprec, steps, stream, flush, over=None):
+    over = over or {}
+    rk104 = over.get("rk") == TEUK_RK_SSP104
+    stages = 10 if rk104 else 3
+    h = teuk_create(params_from_workload(wl, wprec=wprec, **over), stream)
+    _, dt, _ = teuk_get_info(h)
     teuk_set_state(h, I.initial_data(wl), 0.0)
     for _ in range(3):
         teuk_step(h, 1)
@@ -47,8 +65,8 @@ def time_case(torch, wl, wprec, steps, stream, flush):
     stream.synchronize()
     h.close()
     ms = np.mean([a.elapsed_time(b) for a, b in ev])
-    rate = wl.nr * wl.nth * 3 / (ms * 1e-3)
-    return rate, ms, rate * bytes_per_point_stage(wl) / 1e9
+    rate = wl.nr * wl.nth * stages / (ms * 1e-3)
+    return rate, ms, rate * bytes_per_point_stage(wl, rk104) / 1e9, dt / (ms * 1e-3)
 
 
 def main(argv=None):
@@ -58,11 +76,13 @@ def main(argv=None):
     args = ap.parse_args(argv)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    print(f"{'workload':34s} {'weights':7s} {'pt-stage/s':>11s} {'ms/step':>9s} {'HBM GB/s':>9s}")
-    for wl, formats in CASES:
+    print(f"{'workload':44s} {'weights':7s} {'pt-stage/s':>11s} {'ms/step':>9s} {'HBM GB/s':>9s}"
+          f" {'M/s':>9s}")
+    for wl, formats, over, label in CASES:
         for wprec in formats:
-            rate, ms, gbs = time_case(torch, wl, wprec, args.steps, stream, flush)
-            print(f"{wl.name:34s} {wprec:7s} {rate:11.4g} {ms:9.4f} {gbs:9.1f}", flush=True)
+            rate, ms, gbs, mps = time_case(torch, wl, wprec, args.steps, stream, flush, over)
+            print(f"{wl.name + label:44s} {wprec:7s} {rate:11.4g} {ms:9.4f} {gbs:9.1f} {mps:9.1f}",
+                  flush=True)
 
 
 if __name__ == "__main__":
