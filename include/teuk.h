@@ -123,13 +123,14 @@ typedef enum {
 } teuk_field;
 
 /* Problem statement (Sec. 2.1-2.3, Sec. 4): grid, domain, black hole, mode.
- * Valid ranges: nr >= 7, ntheta >= 5, rstar_max > rstar_min, M > 0,
- * 0 <= |a| <= M, s in {-2..2}, |m| <= 64, eps in [1e-60, 1],
+ * Valid ranges: nr >= 7, 5 <= ntheta <= 262140 (four theta rows per CTA,
+ * at most 65535 CTAs along theta), nr*ntheta <= 4e9, rstar_max > rstar_min,
+ * M > 0, 0 <= |a| <= M, s in {-2..2}, |m| <= 64, eps in [1e-60, 1],
  * dt > 0, or dt == 0 with cfl in (0, 1] (dt from the stability rule below).
  * TEUK_COORDS_HYPERBOLOIDAL: hyp_S in [M, 1e6 M], and
  * rho_+ <= rstar_min < rstar_max <= S (rho_+ = r_+ S/(r_+ + S), r_+ = M +
- * sqrt(M^2 - a^2); a bound within 1e-12 relative of rho_+ or S counts as it);
- * rstar_min == rstar_max == 0 selects the whole range [rho_+, S]. */
+ * sqrt(M^2 - a^2); a bound within 1e-12 relative of rho_+ or S counts as it).
+ * Anything else returns TEUK_ERR_ARG. */
 typedef struct {
     int nr, ntheta;                 /* grid nodes in x and theta             */
     double rstar_min, rstar_max;    /* x domain (r* or rho) in units of M    */

@@ -303,6 +303,8 @@ teuk_status teuk_check_params(const teuk_params* p) {
     if (!p) return fail(TEUK_ERR_ARG, "params is NULL");
     if (p->nr < 7) return fail(TEUK_ERR_ARG, "nr must be >= 7 (WENO5 stencil)");
     if (p->ntheta < 5) return fail(TEUK_ERR_ARG, "ntheta must be >= 5");
+    if (p->ntheta > 4 * 65535)      // four theta rows per CTA, grid y <= 65535
+        return fail(TEUK_ERR_ARG, "ntheta must be <= 262140");
     if ((double)p->nr * p->ntheta > 4.0e9)
         return fail(TEUK_ERR_ARG, "grid larger than 4e9 nodes");
     if (!(p->rstar_max > p->rstar_min) || !std::isfinite(p->rstar_min) ||

@@ -32,10 +32,15 @@ def test_status_strings():
     assert T.teuk_status_str(7) == "unknown status"
 
 
+def test_check_params_limits_are_inclusive():
+    assert T.teuk_check_params(T.make_params(7, 262140)) == T.TEUK_OK
+    assert T.teuk_check_params(T.make_params(7, 5)) == T.TEUK_OK
+
+
 @pytest.mark.parametrize("field,value", [("nr", 6), ("ntheta", 4), ("a", 1.5), ("M", 0.0),
                                          ("s", 3), ("eps", 0.0), ("wprec", 7), ("cfl", 0.0),
                                          ("rstar_max", -200.0), ("dt", -1.0), ("theta_mode", 9),
-                                         ("m", 65)])
+                                         ("m", 65), ("ntheta", 262141)])
 def test_check_params_rejects(field, value):
     p = T.make_params(64, 16)
     setattr(p, field, value)
