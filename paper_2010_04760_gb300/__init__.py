@@ -117,7 +117,9 @@ def _check(st):
         raise TeukError(st, msg)
 
 
-def _dptr(x):
+def _dptr(x, need=0, what="device array"):
+    """Device pointer of a CUDA float64 tensor holding at least `need` values
+    (checked), or of a raw integer pointer (the caller vouches for its size)."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -125,8 +127,32 @@ def _dptr(x):
     if hasattr(x, "data_ptr"):
         if not x.is_cuda or x.dtype.__str__() != "torch.float64" or not x.is_contiguous():
             raise ValueError("device arrays must be contiguous CUDA float64 tensors")
+        if x.numel() < need:
+            raise ValueError(f"{what}: needs {need} float64 values, the tensor has {x.numel()}")
         return ctypes.c_void_p(x.data_ptr())
     raise TypeError("expected a CUDA tensor or an integer device pointer")
+
+
+def _nodes(p):
+    return int(p.nr) * int(p.ntheta)
+
+
+def _host_in(a, n, what):
+    """A C-contiguous float64 view or copy of host array a, which must hold
+    exactly n values (the library reads n)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"{what}: expected {n} float64 values, got {a.size}")
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _host_out(out, n, what):
+    """Check a caller's output array: writable C-contiguous float64 of n values."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.flags.writeable and out.size == n):
+        raise ValueError(f"{what}: out must be a writable C-contiguous float64 array of "
+                         f"{n} values")
+    return out.ctypes.data_as(ctypes.c_void_p)
 
 
 def _stream(s):
@@ -135,11 +161,6 @@ def _stream(s):
     if isinstance(s, int):
         return ctypes.c_void_p(s)
     return ctypes.c_void_p(s.cuda_stream)
-
-
-def _host(a):
-    a = np.ascontiguousarray(a, dtype=np.float64)
-    return a, a.ctypes.data_as(ctypes.c_void_p)
 
 
 def horizon_rho(M, a, S):
@@ -209,13 +230,18 @@ def teuk_build_coefficients(p, dt):
 
 
 def teuk_stage_dev(p, dt, coef_dev, u_n, u_prev, u_out, stage, stream=None):
-    _check(lib().teuk_stage_dev(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_n), _dptr(u_prev),
-                                _dptr(u_out), int(stage), _stream(stream)))
+    n, nc = 4 * _nodes(p), teuk_coeff_count(p)
+    _check(lib().teuk_stage_dev(ctypes.byref(p), dt, _dptr(coef_dev, nc, "coef_dev"),
+                                _dptr(u_n, n, "u_n"), _dptr(u_prev, n, "u_prev"),
+                                _dptr(u_out, n, "u_out"), int(stage), _stream(stream)))
 
 
 def teuk_step_dev(p, dt, coef_dev, u_dev, work_dev, nsteps, stream=None):
-    _check(lib().teuk_step_dev(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_dev),
-                               _dptr(work_dev), int(nsteps), _stream(stream)))
+    n, nc = 4 * _nodes(p), teuk_coeff_count(p)
+    scratch = 3 if p.rk == TEUK_RK_SSP104 else 2
+    _check(lib().teuk_step_dev(ctypes.byref(p), dt, _dptr(coef_dev, nc, "coef_dev"),
+                               _dptr(u_dev, n, "u_dev"), _dptr(work_dev, scratch * n, "work_dev"),
+                               int(nsteps), _stream(stream)))
 
 
 def teuk_fp64_fma_rate(stream=None):
@@ -231,8 +257,10 @@ TEUK_STATIC_MAX_NODES = 131072
 def teuk_step_dev_static(p, dt, coef_dev, u_dev, nsteps, stream=None):
     """teuk_step_dev without caller scratch: the stage buffers are a fixed
     array inside the library (grids up to TEUK_STATIC_MAX_NODES nodes)."""
-    _check(lib().teuk_step_dev_static(ctypes.byref(p), dt, _dptr(coef_dev), _dptr(u_dev),
-                                      int(nsteps), _stream(stream)))
+    _check(lib().teuk_step_dev_static(ctypes.byref(p), dt,
+                                      _dptr(coef_dev, teuk_coeff_count(p), "coef_dev"),
+                                      _dptr(u_dev, 4 * _nodes(p), "u_dev"), int(nsteps),
+                                      _stream(stream)))
 
 
 class Handle:
@@ -274,6 +302,8 @@ def teuk_set_initial(h, psi, pi):
     """psi, pi: complex arrays [ntheta, nr]."""
     ps = np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
     pc = np.ascontiguousarray(np.asarray(pi, dtype=np.complex128))
+    if ps.size != _nodes(h.p) or pc.size != _nodes(h.p):
+        raise ValueError(f"psi and pi need {_nodes(h.p)} complex values each")
     _check(lib().teuk_set_initial(h.ptr, ps.ctypes.data_as(ctypes.c_void_p),
                                   pc.ctypes.data_as(ctypes.c_void_p)))
 
@@ -292,15 +322,16 @@ def teuk_set_gaussian(h, rc, width, coeffs=None, nl=None, seed=0):
 
 
 def teuk_set_state(h, u, t=0.0):
-    arr, ptr = _host(u)
+    arr, ptr = _host_in(u, 4 * _nodes(h.p), "teuk_set_state")
     _check(lib().teuk_set_state(h.ptr, ptr, float(t)))
 
 
 def teuk_get_state(h, out=None):
     if out is None:
         out = np.empty((4, h.p.ntheta, h.p.nr))
+    ptr = _host_out(out, 4 * _nodes(h.p), "teuk_get_state")
     t = ctypes.c_double()
-    _check(lib().teuk_get_state(h.ptr, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t)))
+    _check(lib().teuk_get_state(h.ptr, ptr, ctypes.byref(t)))
     return out, t.value
 
 
@@ -311,16 +342,16 @@ def teuk_set_state_async(h, u, t=0.0):
     if arr is not u:
         raise ValueError("teuk_set_state_async needs a C-contiguous float64 array "
                          "(a temporary copy would be freed before the copy runs)")
+    if arr.size != 4 * _nodes(h.p):
+        raise ValueError(f"teuk_set_state_async: expected {4 * _nodes(h.p)} values")
     _check(lib().teuk_set_state_async(h.ptr, arr.ctypes.data_as(ctypes.c_void_p), float(t)))
 
 
 def teuk_get_state_async(h, out):
     """Enqueue the device-to-host copy of the state into out (defined after
     teuk_synchronize)."""
-    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
-            and out.size == 4 * h.p.ntheta * h.p.nr):
-        raise ValueError("out must be a C-contiguous float64 array of 4*ntheta*nr values")
-    _check(lib().teuk_get_state_async(h.ptr, out.ctypes.data_as(ctypes.c_void_p)))
+    ptr = _host_out(out, 4 * _nodes(h.p), "teuk_get_state_async")
+    _check(lib().teuk_get_state_async(h.ptr, ptr))
 
 
 def teuk_synchronize(h):
@@ -381,18 +412,24 @@ def teuk_batch_destroy(b):
     b.close()
 
 
+def _member(b, k):
+    if not 0 <= int(k) < len(b.ps):
+        raise IndexError(f"member {k} of a batch of {len(b.ps)}")
+    return b.ps[int(k)]
+
+
 def teuk_batch_set_state(b, k, u, t=0.0):
-    arr, ptr = _host(u)
+    arr, ptr = _host_in(u, 4 * _nodes(_member(b, k)), "teuk_batch_set_state")
     _check(lib().teuk_batch_set_state(b.ptr, int(k), ptr, float(t)))
 
 
 def teuk_batch_get_state(b, k, out=None):
-    p = b.ps[k]
+    p = _member(b, k)
     if out is None:
         out = np.empty((4, p.ntheta, p.nr))
+    ptr = _host_out(out, 4 * _nodes(p), "teuk_batch_get_state")
     t = ctypes.c_double()
-    _check(lib().teuk_batch_get_state(b.ptr, int(k), out.ctypes.data_as(ctypes.c_void_p),
-                                      ctypes.byref(t)))
+    _check(lib().teuk_batch_get_state(b.ptr, int(k), ptr, ctypes.byref(t)))
     return out, t.value
 
 

@@ -325,6 +325,20 @@ def test_device_entry_points_reject_bad_arguments():
         assert ei.value.status == T.TEUK_ERR_ARG
     with pytest.raises(T.TeukError):
         T.teuk_stage_dev(p, 0.1, coef, None, u, u, 1)       # out aliases u_prev
+    # arrays too small for the grid are refused by the binding before the call
+    short = torch.zeros(4 * 8 * 64 - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        T.teuk_stage_dev(p, 0.1, coef, None, u, short, 1)
+    with pytest.raises(ValueError):
+        T.teuk_stage_dev(p, 0.1, coef[:-1], None, u, out, 1)
+    with pytest.raises(ValueError):
+        T.teuk_step_dev(p, 0.1, coef, u, short, 1)
+    h = T.teuk_create(p)
+    with pytest.raises(ValueError):
+        T.teuk_set_state(h, np.zeros((4, 8, 63)))
+    with pytest.raises(ValueError):
+        T.teuk_get_state(h, np.zeros((4, 8, 63)))
+    h.close()
 
 
 @pytest.mark.parametrize("a,s,m", [(0.999, -2, 2), (0.0, 0, 0), (0.5, -1, 3)])

@@ -306,3 +306,45 @@ def test_host_allocation_failure_is_a_status():
     assert int(st) == T.TEUK_ERR_HOST
     assert handle == "None"
     assert msg == "teuk_create: host memory exhausted"
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA float64 tensor in the binding's argument checks."""
+
+    def __init__(self, n, dtype="torch.float64", cuda=True, contiguous=True):
+        self.n, self.dtype, self.is_cuda, self._c = n, dtype, cuda, contiguous
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        return 0x1000
+
+
+def test_binding_checks_array_sizes_before_calling_the_library():
+    """The binding refuses arrays that are too small (or of the wrong kind)
+    before any pointer reaches the library, so a size mistake in Python is
+    an exception, never an access outside a buffer."""
+    assert T._dptr(_FakeCudaTensor(10), 10).value == 0x1000
+    with pytest.raises(ValueError, match="needs 11"):
+        T._dptr(_FakeCudaTensor(10), 11, "u_out")
+    for bad in (_FakeCudaTensor(10, dtype="torch.float32"), _FakeCudaTensor(10, cuda=False),
+                _FakeCudaTensor(10, contiguous=False)):
+        with pytest.raises(ValueError):
+            T._dptr(bad, 1)
+    assert T._dptr(12345, 10**9).value == 12345          # raw pointers: the caller's word
+    a, _ = T._host_in(np.zeros((4, 3, 7)), 84, "u")
+    assert a.size == 84
+    with pytest.raises(ValueError, match="expected 84"):
+        T._host_in(np.zeros((4, 3, 6)), 84, "u")
+    T._host_out(np.zeros((4, 3, 7)), 84, "out")
+    for bad in (np.zeros(83), np.zeros(84, dtype=np.float32), np.zeros((84, 2))[:, 0]):
+        with pytest.raises(ValueError):
+            T._host_out(bad, 84, "out")
+    ro = np.zeros(84)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        T._host_out(ro, 84, "out")
