@@ -22,7 +22,9 @@
  * that the reading is the paper's formula rearranged).
  *
  * Parity status: every routine is pinned by the tests in tests/test_oracle_pins.py,
- * tests/test_oracle_physics.py and tests/test_oracle_hyperboloidal.py, except the
+ * tests/test_oracle_physics.py and tests/test_oracle_hyperboloidal.py (and
+ * tests/test_oracle_mutants.py shows that single-edit mistakes planted in each
+ * routine of a copy of teuk_oracle.c make those pins fail), except the
  * Aretakis-charge interpretation of the horizon gather in r*, which is "parity
  * unpinned" (the extremal horizon is not on an r* grid). On the hyperboloidal
  * grid the horizon is node 0 and the Aretakis laws are pinned.
