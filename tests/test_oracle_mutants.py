@@ -197,6 +197,22 @@ MUTANTS = [
     ("observe: horizon gather one node in", "horizon[6 * j + c] = u[c * plane + row];",
      "horizon[6 * j + c] = u[c * plane + row + 1];",
      [PH + "test_observe_gathers_nodes_and_one_sided_derivative"]),
+    ("FD6 on the slices with edge-copy ghosts",
+     "g->coords == 1 ? 2 : 0, &Dc[c * nr], &Qc[c * nr]);", "0, &Dc[c * nr], &Qc[c * nr]);",
+     [ASSEMBLY]),
+    ("WENO on the slices with edge-copy ghosts",
+     "g->eps, g->coords == 1 ? 2 : 0, NULL, &Dc[c * nr],", "g->eps, 0, NULL, &Dc[c * nr],",
+     [ASSEMBLY]),
+    ("theta WENO: pole ghost mirrored on the node",
+     "if (jj < 0) { jj = -1 - jj; sg = sigma; }\n                    if (jj >= nth)",
+     "if (jj < 0) { jj = -jj; sg = sigma; }\n                    if (jj >= nth)",
+     [PH + "test_theta_weno_option_on_spin_weighted_harmonics"]),
+    ("theta WENO: direction from Ath instead of Bth", "double Bth_here = coef[8 * plane + p];",
+     "double Bth_here = coef[7 * plane + p];", [PH + "test_theta_weno_stencil_lies_upwind"]),
+    ("theta WENO: flux difference over 2 dtheta", "d[c] = (fp - fm) / dth;",
+     "d[c] = (fp - fm) / (2.0 * dth);", [PH + "test_theta_weno_option_on_spin_weighted_harmonics"]),
+    ("hyperboloidal db/drho: a real-size complex step", "double hstep = 1e-30;",
+     "double hstep = 1e-2;", [SYM_HYP]),
     # observation, Sec. 4
     ("observe: one-sided derivative over h", "horizon[6 * j + 4 + c] = (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * h);",
      "horizon[6 * j + 4 + c] = (-3.0 * f[0] + 4.0 * f[1] - f[2]) / h;",
