@@ -348,3 +348,39 @@ def test_binding_checks_array_sizes_before_calling_the_library():
     ro.flags.writeable = False
     with pytest.raises(ValueError):
         T._host_out(ro, 84, "out")
+
+
+def test_missing_library_fails_loudly_with_no_cpu_fallback(tmp_path):
+    """Without the CUDA library every binding call raises; nothing computes on
+    the CPU in its place."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import sys; sys.path.insert(0, sys.argv[1])\n"
+        "import paper_2010_04760_gb300 as T\n"
+        "T.LIB_PATH = sys.argv[2]\n"
+        "try:\n"
+        "    T.teuk_check_params(T.make_params(16, 8))\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    print('no error')\n")
+    out = subprocess.run([sys.executable, "-c", child, root, str(tmp_path / "absent.so")],
+                         capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("raised:") and "no CPU fallback" in out.stdout
+
+
+def test_product_code_never_touches_the_oracle():
+    """The library, its binding and the input module neither import, load nor
+    name the oracle package (the oracle is test infrastructure)."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2010_04760_gb300")
+    pat = re.compile(r"(import\s+oracle|from\s+oracle|teuk_oracle|orc_|libteuk_oracle)")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not pat.search(text), os.path.join(dirpath, f)
