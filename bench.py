@@ -296,7 +296,7 @@ def time_paper_run(T, torch, stream, steps=200):
             "finite": st == T.TEUK_OK}
 
 
-def oracle_rate(nsteps_budget_s=12.0, wprec="fp32", max_steps=400):
+def oracle_rate(nsteps_budget_s=15.0, wprec="fp32", max_steps=1000):
     """Oracle point-stage updates/s on the workload, over a bounded number of
     RK steps chosen to take about nsteps_budget_s seconds."""
     import oracle as o
