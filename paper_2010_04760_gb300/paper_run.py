@@ -8,6 +8,8 @@ prints, every `every` M of tau, Phi and dPhi/drho on the horizon (the
 Aretakis observables of Sec. 4, middle theta row), Phi at scri and the local
 decay index tau dPhi/dtau / Phi on the horizon, then the throughput of the
 stepping in point-stage updates per second. Runs on cuda:0 through the C ABI.
+`--scheme fd6` runs the paper's comparison scheme instead (sixth-order centred
+differences with Kreiss-Oliger dissipation of strength `--sigma`, Sec. 3.1.1).
 """
 import argparse
 import time
@@ -16,7 +18,7 @@ import numpy as np
 
 from . import inputs as I
 from . import teuk_create, teuk_get_info, teuk_observe, teuk_set_state, teuk_step
-from . import params_from_workload
+from . import TEUK_SCHEME_FD6_KO8, TEUK_SCHEME_WENO5, params_from_workload
 
 
 def main(argv=None):
@@ -28,16 +30,21 @@ def main(argv=None):
     ap.add_argument("--tau", type=float, default=50.0, help="final tau (units of M)")
     ap.add_argument("--steps", type=int, default=0, help="run this many steps instead")
     ap.add_argument("--every", type=float, default=10.0, help="observation interval in tau")
+    ap.add_argument("--scheme", default="weno5", choices=["weno5", "fd6"],
+                    help="radial scheme: WENO5 or FD6 + Kreiss-Oliger")
+    ap.add_argument("--sigma", type=float, default=0.01, help="Kreiss-Oliger sigma (fd6)")
     args = ap.parse_args(argv)
 
     wl = I.EXTREMAL_GRAV_HYP.with_(nr=args.nr, nth=args.nth, wprec=args.wprec)
-    h = teuk_create(params_from_workload(wl))
+    scheme = TEUK_SCHEME_FD6_KO8 if args.scheme == "fd6" else TEUK_SCHEME_WENO5
+    h = teuk_create(params_from_workload(wl, scheme=scheme, ko_sigma=args.sigma))
     teuk_set_state(h, I.initial_data(wl), 0.0)
     _, dt, _ = teuk_get_info(h)
     total = args.steps if args.steps > 0 else int(np.ceil(args.tau / dt))
     chunk = max(1, min(total, int(round(args.every / dt))))
     j = wl.nth // 2
-    print(f"# {wl.name}: {wl.nr} x {wl.nth}, weights {wl.wprec}, dt = {dt:.6g} M, {total} steps")
+    label = f"FD6 + KO8 (sigma {args.sigma:g})" if args.scheme == "fd6" else f"weights {wl.wprec}"
+    print(f"# {wl.name}: {wl.nr} x {wl.nth}, {label}, dt = {dt:.6g} M, {total} steps")
     print("#      tau        Phi_H     dPhi_H/drho     Phi_scri    p(Phi_H)")
     done, prev, stepping = 0, None, 0.0
     while done < total:
