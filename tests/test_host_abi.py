@@ -147,6 +147,28 @@ def _check_planes_against_oracle(p, co, dt, coords):
     if coords == 1:
         np.testing.assert_allclose(got[12], dt * c / (6 * h), rtol=1e-9, atol=1e-14)
         assert np.all(got[11] == 0.0)
+    _check_theta_planes(got, co, p.s, p.m, dt)
+
+
+def _check_theta_planes(got, co, s, m, dt):
+    """The five theta planes applied to a field with the pole parity give
+    dt (Ath Psi_thth + Bth Psi_th + Re C Psi) of the oracle's ghost-row
+    operator (fourth-order centred differences)."""
+    nth, nr = got.shape[1:]
+    Cr, Ath, Bth = co[5], co[7], co[8]
+    dth = np.pi / nth
+    psi = np.random.default_rng(0).standard_normal((nth, nr))
+    sig = 1.0 if (m + s) % 2 == 0 else -1.0
+    acc = np.zeros((nth, nr))
+    for k in range(-2, 3):
+        rows = np.clip(np.arange(nth) + k, 0, nth - 1)
+        acc += got[8 + k] * psi[rows]
+    ext = np.concatenate([sig * psi[1::-1], psi, sig * psi[:-3:-1]])   # rows -2..nth+1
+    nb = [ext[2 + k:2 + k + nth] for k in range(-2, 3)]
+    th1 = (nb[0] - 8 * nb[1] + 8 * nb[3] - nb[4]) / (12 * dth)
+    th2 = (-nb[0] + 16 * nb[1] - 30 * nb[2] + 16 * nb[3] - nb[4]) / (12 * dth ** 2)
+    exp_ = dt * (Ath * th2 + Bth * th1 + Cr * psi)
+    np.testing.assert_allclose(acc, exp_, rtol=1e-8, atol=1e-10 * np.max(np.abs(exp_)))
 
 
 @pytest.mark.parametrize("a,s,m", [(0.0, 0, 0), (1.0, -2, 0), (0.7, -2, 2), (0.3, 1, -1),
