@@ -129,7 +129,9 @@ typedef enum {
  * dt > 0, or dt == 0 with cfl in (0, 1] (dt from the stability rule below).
  * TEUK_COORDS_HYPERBOLOIDAL: hyp_S in [M, 1e6 M], and
  * rho_+ <= rstar_min < rstar_max <= S (rho_+ = r_+ S/(r_+ + S), r_+ = M +
- * sqrt(M^2 - a^2); a bound within 1e-12 relative of rho_+ or S counts as it).
+ * sqrt(M^2 - a^2); a bound within 1e-12 relative of rho_+ or S counts as it),
+ * or rstar_min == rstar_max == 0, which every call reads as the whole slice
+ * [rho_+, S] (teuk_get_info returns the filled-in range).
  * Anything else returns TEUK_ERR_ARG. */
 typedef struct {
     int nr, ntheta;                 /* grid nodes in x and theta             */
@@ -164,6 +166,12 @@ const char* teuk_last_error(void);
 
 /* Validate p (see teuk_params). Returns TEUK_OK or TEUK_ERR_ARG. */
 teuk_status teuk_check_params(const teuk_params* p);
+
+/* rho of the outer horizon on the hyperboloidal slices of Sec. 2.2:
+ * rho_+ = r_+ S/(r_+ + S), r_+ = M + sqrt(M^2 - a^2) (the slice's rho =
+ * r/(1 + r/S) at the horizon radius). Needs M > 0, |a| <= M, S in
+ * [M, 1e6 M]; TEUK_ERR_ARG otherwise. */
+teuk_status teuk_horizon_rho(double M, double a, double S, double* rho_out);
 
 /* Time step of the stability rule used when p->dt == 0:
  *   dt = cfl / max_ij [ max(|b|, |c|)/h + sqrt(kappa) ],

@@ -65,6 +65,7 @@ def lib():
             "teuk_status_str": (ctypes.c_char_p, [I]),
             "teuk_last_error": (ctypes.c_char_p, []),
             "teuk_check_params": (I, [PP]),
+            "teuk_horizon_rho": (I, [D, D, D, P]),
             "teuk_stable_dt": (I, [PP, P]),
             "teuk_coeff_count": (S, [PP]),
             "teuk_build_coefficients": (I, [PP, D, P]),
@@ -163,22 +164,17 @@ def _stream(s):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def horizon_rho(M, a, S):
-    """rho of the outer horizon on the hyperboloidal slices, r_+ S/(r_+ + S)."""
-    rp = M + (max(M * M - a * a, 0.0)) ** 0.5
-    return rp * S / (rp + S)
-
-
 def make_params(nr, ntheta, rstar_min=None, rstar_max=None, M=1.0, a=0.0, s=0, m=0,
                 cfl=0.5, dt=0.0, eps=1e-6, wprec="fp64", theta_mode=TEUK_THETA_CENTERED4,
                 rk=TEUK_RK_SSP33, scheme=TEUK_SCHEME_WENO5, ko_sigma=0.01,
                 coords=TEUK_COORDS_RSTAR, field=None, hyp_S=20.0):
     """teuk_params with defaults: r* in [-100, 300] M; on the hyperboloidal
-    slices the whole range [rho_+, S] and the field Phi."""
+    slices the whole range [rho_+, S] (rho_+ from the library) and the field
+    Phi."""
     w = WPREC[wprec] if isinstance(wprec, str) else int(wprec)
     hyp = coords == TEUK_COORDS_HYPERBOLOIDAL
     if rstar_min is None:
-        rstar_min = horizon_rho(M, a, hyp_S) if hyp else -100.0
+        rstar_min = teuk_horizon_rho(M, a, hyp_S) if hyp else -100.0
     if rstar_max is None:
         rstar_max = hyp_S if hyp else 300.0
     if field is None:
@@ -208,6 +204,16 @@ def teuk_last_error():
 
 def teuk_check_params(p):
     return lib().teuk_check_params(ctypes.byref(p))
+
+
+def teuk_horizon_rho(M, a, S):
+    """rho of the outer horizon on the hyperboloidal slices."""
+    out = ctypes.c_double()
+    _check(lib().teuk_horizon_rho(float(M), float(a), float(S), ctypes.byref(out)))
+    return out.value
+
+
+horizon_rho = teuk_horizon_rho
 
 
 def teuk_stable_dt(p):

@@ -172,6 +172,8 @@ teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_d
     return guarded("teuk_stage_dev", [&]() -> teuk_status {
         teuk_status st = teuk_check_params(p);
         if (st != TEUK_OK) return st;
+        const teuk_params q = resolve_params(*p);
+        p = &q;
         if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
         if (stage < 0 || stage > 3) return fail(TEUK_ERR_ARG, "stage must be 0..3");
         if (!coef_dev || !u_prev || !u_out) return fail(TEUK_ERR_ARG, "NULL device pointer");
@@ -191,6 +193,8 @@ teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_de
         NvtxRange trace("teuk_step_dev");
         teuk_status st = teuk_check_params(p);
         if (st != TEUK_OK) return st;
+        const teuk_params q = resolve_params(*p);
+        p = &q;
         if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
         if (!coef_dev || !u_dev || !work_dev) return fail(TEUK_ERR_ARG, "NULL device pointer");
         if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
@@ -218,6 +222,8 @@ teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* 
     return guarded("teuk_step_dev_static", [&]() -> teuk_status {
         teuk_status st = teuk_check_params(p);
         if (st != TEUK_OK) return st;
+        const teuk_params q = resolve_params(*p);
+        p = &q;
         const size_t nodes = (size_t)p->nr * p->ntheta;
         if (nodes > (size_t)TEUK_STATIC_MAX_NODES)
             return fail(TEUK_ERR_ARG, "grid has " + std::to_string(nodes) +
@@ -334,7 +340,8 @@ teuk_status teuk_batch_create(const teuk_params* ps, int n, void* stream, int au
         teuk_batch* b = own.b;
         b->n = n;
         b->wprec = ps[0].wprec;
-        b->p.assign(ps, ps + n);
+        b->p.resize(n);
+        for (int k = 0; k < n; ++k) b->p[k] = resolve_params(ps[k]);
         b->dt.resize(n);
         b->t.assign(n, 0.0);
         b->off.resize(n);
@@ -517,7 +524,7 @@ teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
         st = teuk_build_coefficients(p, dt, coef.data());
         if (st != TEUK_OK) return st;
         teuk_handle* h = new teuk_handle();
-        h->p = *p;
+        h->p = resolve_params(*p);
         h->dt = dt;
         cudaError_t e = cudaSuccess;
         if (stream) {

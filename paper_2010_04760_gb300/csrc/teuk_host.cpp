@@ -206,6 +206,18 @@ double horizon_rho(double M, double a, double S) {
     return rp * S / (rp + S);
 }
 
+// On the hyperboloidal slices a range given as [0, 0] stands for the whole
+// slice, from the outer horizon rho_+ to scri (rho = S).
+teuk_params resolve_params(const teuk_params& p) {
+    teuk_params q = p;
+    if (q.coords == TEUK_COORDS_HYPERBOLOIDAL && q.rstar_min == 0.0 && q.rstar_max == 0.0 &&
+        q.M > 0.0 && std::fabs(q.a) <= q.M && q.hyp_S > 0.0) {
+        q.rstar_min = horizon_rho(q.M, q.a, q.hyp_S);
+        q.rstar_max = q.hyp_S;
+    }
+    return q;
+}
+
 // Spin-weighted spherical harmonic sY_lm(theta, phi = 0), Goldberg et al.
 // (1967): (-1)^m sqrt[(l+m)!(l-m)!(2l+1) / (4 pi (l+s)!(l-s)!)]
 //   x sum_r C(l-s, r) C(l+s, r+s-m) (-1)^(l-r-s) sin^(2l-k)(th/2) cos^k(th/2),
@@ -299,8 +311,19 @@ const char* teuk_status_str(teuk_status st) {
 
 const char* teuk_last_error(void) { return g_last_error.c_str(); }
 
+teuk_status teuk_horizon_rho(double M, double a, double S, double* rho_out) {
+    if (!rho_out) return fail(TEUK_ERR_ARG, "rho_out is NULL");
+    if (!(M > 0.0) || !std::isfinite(M)) return fail(TEUK_ERR_ARG, "need M > 0");
+    if (!(std::fabs(a) <= M)) return fail(TEUK_ERR_ARG, "need |a| <= M");
+    if (!(S >= M && S <= 1e6 * M)) return fail(TEUK_ERR_ARG, "S must be in [M, 1e6 M]");
+    *rho_out = horizon_rho(M, a, S);
+    return TEUK_OK;
+}
+
 teuk_status teuk_check_params(const teuk_params* p) {
     if (!p) return fail(TEUK_ERR_ARG, "params is NULL");
+    const teuk_params q = resolve_params(*p);
+    p = &q;
     if (p->nr < 7) return fail(TEUK_ERR_ARG, "nr must be >= 7 (WENO5 stencil)");
     if (p->ntheta < 5) return fail(TEUK_ERR_ARG, "ntheta must be >= 5");
     if (p->ntheta > 4 * 65535)      // four theta rows per CTA, grid y <= 65535
@@ -353,6 +376,8 @@ teuk_status teuk_stable_dt(const teuk_params* p, double* dt_out) {
         teuk_status st = teuk_check_params(p);
         if (st != TEUK_OK) return st;
         if (!dt_out) return fail(TEUK_ERR_ARG, "dt_out is NULL");
+        const teuk_params q = resolve_params(*p);
+        p = &q;
         if (p->dt > 0.0) { *dt_out = p->dt; return TEUK_OK; }
         const double h = (p->rstar_max - p->rstar_min) / (p->nr - 1);
         const double dth = M_PI / p->ntheta;
@@ -391,6 +416,8 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
         teuk_status st = teuk_check_params(p);
         if (st != TEUK_OK) return st;
         if (!coef) return fail(TEUK_ERR_ARG, "coef_host is NULL");
+        const teuk_params q = resolve_params(*p);
+        p = &q;
         if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TEUK_ERR_ARG, "dt must be > 0");
         const int nr = p->nr, nth = p->ntheta;
         const size_t plane = (size_t)nr * nth;

@@ -66,6 +66,8 @@ PointCoef point_coefficients(double rstar, double theta, const teuk_params& p);
 PointCoef point_coefficients_rx(double r, double x, double theta, const teuk_params& p);
 PointCoef point_coefficients_hyp(double rho, double theta, const teuk_params& p);
 double horizon_rho(double M, double a, double S);
+// p with a hyperboloidal range given as [0, 0] replaced by [rho_+, S].
+teuk_params resolve_params(const teuk_params& p);
 
 double swsh(int s, int l, int m, double theta);
 uint64_t splitmix64(uint64_t& state);

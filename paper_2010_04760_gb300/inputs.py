@@ -157,6 +157,18 @@ def random_state(nr, nth, seed, smooth=True):
     return u
 
 
+def multiscale_state(nr, nth, seed, smooth=True):
+    """random_state with every theta row scaled by 10^U(-40, 6) and the first
+    nr/8 radial nodes by a further 1e-200: regions where epsilon dominates the
+    smoothness indicators and where the reduced-precision weights need their
+    scaling into range."""
+    u = random_state(nr, nth, seed, smooth=smooth)
+    rng = np.random.default_rng(seed + 100)
+    u = u * 10.0 ** rng.uniform(-40, 6, size=(1, nth, 1))
+    u[:, :, : nr // 8] *= 1e-200
+    return u
+
+
 # ---------------------------------------------------------------------------
 # Named workloads (sizes, physics and data of the benchmark suite).
 # ---------------------------------------------------------------------------

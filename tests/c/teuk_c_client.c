@@ -3,9 +3,12 @@
  * tests/test_host_abi.py (host-side calls, no GPU) and tests/test_gpu_parity.py
  * (the "gpu" mode). It uses nothing but the header's declarations: parameters
  * for the 2048 x 128 Kerr workload, the stability rule and the coefficient
- * array; with "gpu", a handle with the seeded Gaussian initial data, 40 steps
+ * array; the same on the hyperboloidal slices, whose range [0, 0] stands for
+ * the whole slice from the horizon to scri (the client never computes rho_+);
+ * with "gpu", a handle with the seeded Gaussian initial data, 40 steps
  * (graph replay plus direct launches), the observation at r* = 50 M and on the
- * innermost node, and a checkpoint round trip.
+ * innermost node, a checkpoint round trip, and a hyperboloidal handle observed
+ * on the horizon and at scri.
  *
  * Output: "key value" lines read by the tests. Exit status 0 on success.
  */
@@ -51,6 +54,21 @@ static teuk_params kerr_params(void) {
     return p;
 }
 
+/* The paper's extremal run on the hyperboloidal slices (Sec. 4), reduced to
+ * 512 x 16 nodes; range [0, 0]: the library takes [rho_+, S]. */
+static teuk_params hyp_params(void) {
+    teuk_params p = kerr_params();
+    p.nr = 512;
+    p.ntheta = 16;
+    p.rstar_min = 0.0;
+    p.rstar_max = 0.0;
+    p.a = 1.0;
+    p.m = 0;
+    p.coords = TEUK_COORDS_HYPERBOLOIDAL;
+    p.field = TEUK_FIELD_PHI;
+    return p;
+}
+
 static int host_mode(void) {
     teuk_params p = kerr_params();
     CHECK(teuk_check_params(&p));
@@ -72,6 +90,14 @@ static int host_mode(void) {
     teuk_status st = teuk_check_params(&bad);
     printf("bad_status %d\n", (int)st);
     printf("bad_message_nonempty %d\n", teuk_last_error()[0] != '\0');
+    /* the whole hyperboloidal slice without computing rho_+ here */
+    teuk_params q = hyp_params();
+    CHECK(teuk_check_params(&q));
+    double dth = 0.0, rhop = 0.0;
+    CHECK(teuk_stable_dt(&q, &dth));
+    CHECK(teuk_horizon_rho(q.M, q.a, q.hyp_S, &rhop));
+    printf("hyp_dt %.17g\n", dth);
+    printf("horizon_rho %.17g\n", rhop);
     return 0;
 }
 
@@ -107,6 +133,25 @@ static int gpu_mode(void) {
     /* the C ABI reports a bad call through its status */
     printf("neg_steps_status %d\n", (int)teuk_step(h, -1));
     CHECK(teuk_destroy(h));
+    /* a handle on the whole hyperboloidal slice: the library fills the range */
+    teuk_params q = hyp_params();
+    teuk_handle* hh = NULL;
+    CHECK(teuk_create(&q, NULL, &hh));
+    teuk_params got;
+    CHECK(teuk_get_info(hh, &got, NULL, NULL));
+    printf("hyp_range %.17g %.17g\n", got.rstar_min, got.rstar_max);
+    const double c1[2] = {1.0, 0.0};
+    CHECK(teuk_set_gaussian(hh, 1.0, 0.22, c1, 1, 0));
+    CHECK(teuk_step(hh, 20));
+    double* hw = (double*)malloc(2 * (size_t)q.ntheta * sizeof(double));
+    double* hh6 = (double*)malloc(6 * (size_t)q.ntheta * sizeof(double));
+    CHECK(teuk_observe(hh, got.rstar_max, hw, hh6, NULL));
+    double hsum = 0.0;
+    for (int k = 0; k < 6 * q.ntheta; ++k) hsum += fabs(hh6[k]);
+    printf("hyp_horizon_abs_sum %.17g\n", hsum);
+    CHECK(teuk_destroy(hh));
+    free(hw);
+    free(hh6);
     free(wave);
     free(hor);
     free(u0);

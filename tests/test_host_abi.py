@@ -201,7 +201,8 @@ def test_hyperboloidal_argument_rules():
     assert T.teuk_check_params(T.make_params(64, 16, a=0.6, coords=H, scheme=1)) == T.TEUK_OK
     assert T.teuk_check_params(T.make_params(64, 16, a=0.6, coords=H, theta_mode=1)) == T.TEUK_OK
     bad = [dict(field=T.TEUK_FIELD_PSI), dict(scheme=1, theta_mode=1),
-           dict(hyp_S=0.5), dict(rstar_min=rhop * 0.999), dict(rstar_max=20.001),
+           dict(hyp_S=0.5, rstar_min=0.0, rstar_max=0.0), dict(rstar_min=rhop * 0.999),
+           dict(rstar_max=20.001),
            dict(coords=2), dict(field=3)]
     for kw in bad:
         p = T.make_params(64, 16, a=0.6, s=-2, m=1, **{**dict(coords=H), **kw})
@@ -292,6 +293,31 @@ def test_plain_c_client_of_the_abi(tmp_path):
     assert float(got["coef_abs_sum"]) == pytest.approx(np.abs(T.teuk_build_coefficients(p, dt)).sum(),
                                                        rel=1e-12)   # summation order
     assert int(got["bad_status"]) == T.TEUK_ERR_ARG and got["bad_message_nonempty"] == "1"
+    # the whole hyperboloidal slice from the range [0, 0], rho_+ filled in by
+    # the library (the client never computes it)
+    rhop = I.horizon_rho(1.0, 1.0, 20.0)
+    assert float(got["horizon_rho"]) == pytest.approx(rhop, rel=1e-15)
+    q = T.make_params(512, 16, rhop, 20.0, 1.0, 1.0, -2, 0, wprec="fp32",
+                      coords=T.TEUK_COORDS_HYPERBOLOIDAL)
+    assert float(got["hyp_dt"]) == T.teuk_stable_dt(q)
+
+
+def test_hyperboloidal_default_range():
+    """rstar_min == rstar_max == 0 on the hyperboloidal slices is the whole
+    slice [rho_+, S] for every call that takes parameters; in r* it is an
+    empty range and an error."""
+    rhop = T.teuk_horizon_rho(1.0, 0.6, 20.0)
+    assert rhop == pytest.approx(I.horizon_rho(1.0, 0.6, 20.0), rel=1e-15)
+    full = T.make_params(64, 8, rhop, 20.0, 1.0, 0.6, -2, 1, coords=T.TEUK_COORDS_HYPERBOLOIDAL)
+    zero = T.make_params(64, 8, 0.0, 0.0, 1.0, 0.6, -2, 1, coords=T.TEUK_COORDS_HYPERBOLOIDAL)
+    assert T.teuk_check_params(zero) == T.TEUK_OK
+    assert T.teuk_stable_dt(zero) == T.teuk_stable_dt(full)
+    np.testing.assert_array_equal(T.teuk_build_coefficients(zero, 0.01),
+                                  T.teuk_build_coefficients(full, 0.01))
+    assert T.teuk_check_params(T.make_params(64, 8, 0.0, 0.0)) == T.TEUK_ERR_ARG
+    for bad in [(0.0, 1.0, 20.0), (1.0, 1.5, 20.0), (1.0, 0.5, 0.5)]:
+        with pytest.raises(T.TeukError):
+            T.teuk_horizon_rho(*bad)
 
 
 _HOST_OOM_CHILD = r"""

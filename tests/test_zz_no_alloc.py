@@ -2,9 +2,13 @@
 memory (for example code whose device memory all belongs to a framework's
 caching pool, or latency-critical loops where cudaMalloc/cudaFree would
 synchronise the device). Its stage buffers are a fixed array inside the
-library. Two calls in a row, on different grids and data, must give what the
-caller-scratch entry point teuk_step_dev gives, within the parity tolerance
-used by the other GPU tests (1e-12 of the largest magnitude per component)."""
+library. It runs the same kernels on the same inputs as the caller-scratch
+entry point teuk_step_dev, so two calls in a row, on different grids and data,
+must give bitwise what teuk_step_dev gives: a value left in the shared array by
+the previous call and read before being written would show up as a
+difference. After the first call (which may make the CUDA runtime load the
+library's device code and its static array), a call must leave the device's
+free memory unchanged."""
 import numpy as np
 import pytest
 
@@ -13,8 +17,6 @@ from paper_2010_04760_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-TOL = 1e-12
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,27 +38,26 @@ def _reference_and_static(wl, wprec, nsteps, dt):
     work = torch.empty(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
     T.teuk_step_dev(p, dt, coef, u_ref, work, nsteps)
     u_st = _dev(u0)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
     T.teuk_step_dev_static(p, dt, coef, u_st, nsteps)
     torch.cuda.synchronize()
-    return u_ref.cpu().numpy(), u_st.cpu().numpy()
-
-
-def _close(got, ref):
-    for c in range(4):
-        scale = np.max(np.abs(ref[c]))
-        assert np.max(np.abs(got[c] - ref[c])) <= TOL * scale + 1e-300, c
+    free_after = torch.cuda.mem_get_info()[0]
+    return u_ref.cpu().numpy(), u_st.cpu().numpy(), free_before - free_after
 
 
 def test_static_scratch_matches_caller_scratch_two_calls():
     # first call: the 256 x 32 scalar workload, binary32 weights
-    ref, got = _reference_and_static(I.SCHW_SCALAR, "fp32", 7, 0.05)
-    _close(got, ref)
+    ref, got, _ = _reference_and_static(I.SCHW_SCALAR, "fp32", 7, 0.05)
+    np.testing.assert_array_equal(got, ref)
     # second call on the same array: a different grid at the size limit
-    # (1024 x 128 = TEUK_STATIC_MAX_NODES nodes) and different data
+    # (1024 x 128 = TEUK_STATIC_MAX_NODES nodes) and different data; the
+    # array is resident by now, so the call must not take device memory
     wl = I.KERR_GRAV.with_(nr=1024, nth=128, rs_min=-60.0, rs_max=140.0)
     assert wl.nr * wl.nth == T.TEUK_STATIC_MAX_NODES
-    ref, got = _reference_and_static(wl, "fp64", 5, 0.01)
-    _close(got, ref)
+    ref, got, taken = _reference_and_static(wl, "fp64", 5, 0.01)
+    np.testing.assert_array_equal(got, ref)
+    assert taken == 0, f"teuk_step_dev_static took {taken} bytes of device memory"
 
 
 def test_static_scratch_rejects_grids_beyond_the_limit():
