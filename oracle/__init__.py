@@ -60,6 +60,7 @@ def _load():
         sig = {
             "orc_rstar_of_r": (D, [D, D, D]),
             "orc_r_of_rstar": (D, [D, D, D]),
+            "orc_x_of_rstar": (D, [D, D, D]),
             "orc_coeff_point": (None, [D, D, D, D, I, I, I, P]),
             "orc_coeff_point_hyp": (None, [D, D, D, D, D, I, I, P]),
             "orc_rho_of_r": (D, [D, D]),
@@ -123,6 +124,11 @@ def rstar_of_r(r, M=1.0, a=0.0):
 
 def r_of_rstar(rs, M=1.0, a=0.0):
     return _load().orc_r_of_rstar(rs, M, a)
+
+
+def x_of_rstar(rs, M=1.0, a=0.0):
+    """r - r_+ at r* (resolved where it is far below the spacing of r)."""
+    return _load().orc_x_of_rstar(rs, M, a)
 
 
 def coeff_point(r, th, M, a, s, m, field=0):

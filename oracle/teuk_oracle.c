@@ -61,31 +61,45 @@ int orc_num_threads(void) {
 
 /* ------------------------------------------------------------------------ */
 /* Tortoise coordinate, r* = int (r^2+a^2)/Delta dr (Sec. 2.2). Integration  */
-/* constant: the one that makes r* -> r + 2M ln(r/2M - 1) at a = 0.          */
+/* constant: the one that makes r* -> r + 2M ln(r/2M - 1) at a = 0. Written  */
+/* in y = ln(r - r_+): towards the horizon r - r_+ falls off exponentially    */
+/* in r* (e-folding length 2M r_+/(r_+ - r_-)), below the spacing of binary64 */
+/* numbers near r_+ once r* is a few tens of M negative, so r itself cannot  */
+/* carry it and Delta = (r - r_+)(r - r_-) must be formed from r - r_+.       */
 /* ------------------------------------------------------------------------ */
-double orc_rstar_of_r(double r, double M, double a) {
+static double rstar_of_lnx(double y, double M, double a) {
+    double x = exp(y);
     if (fabs(a) < M) {
         double d = sqrt(M * M - a * a);
         double rp = M + d, rm = M - d;
-        return r + (2.0 * M * rp / (rp - rm)) * log((r - rp) / (2.0 * M))
-                 - (2.0 * M * rm / (rp - rm)) * log((r - rm) / (2.0 * M));
+        return rp + x + (2.0 * M * rp / (rp - rm)) * (y - log(2.0 * M))
+                 - (2.0 * M * rm / (rp - rm)) * log((x + rp - rm) / (2.0 * M));
     }
     /* extremal a = M: Delta = (r - M)^2 */
-    return r + 2.0 * M * log((r - M) / M) - 2.0 * M * M / (r - M);
+    return M + x + 2.0 * M * (y - log(M)) - 2.0 * M * M * exp(-y);
 }
 
-/* r(r*) by bisection on the monotone map r -> r*, r in (r_+, infinity). */
-double orc_r_of_rstar(double rs, double M, double a) {
-    double rp = M + sqrt(fmax(M * M - a * a, 0.0));
-    double lo = rp, hi = rp + 1.0;
-    while (orc_rstar_of_r(hi, M, a) < rs) hi = rp + 2.0 * (hi - rp);
+static double horizon_r(double M, double a) { return M + sqrt(fmax(M * M - a * a, 0.0)); }
+
+double orc_rstar_of_r(double r, double M, double a) {
+    return rstar_of_lnx(log(r - horizon_r(M, a)), M, a);
+}
+
+/* r - r_+ at r*, by bisection on y = ln(r - r_+) (y -> r* is monotone). */
+double orc_x_of_rstar(double rs, double M, double a) {
+    double lo = -1.0, hi = 1.0;
+    while (rstar_of_lnx(lo, M, a) > rs && lo > -1.0e6) lo *= 2.0;
+    while (rstar_of_lnx(hi, M, a) < rs) hi *= 2.0;
     for (int it = 0; it < 400; ++it) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        double v = (mid > rp) ? orc_rstar_of_r(mid, M, a) : -INFINITY;
-        if (v < rs) lo = mid; else hi = mid;
+        if (rstar_of_lnx(mid, M, a) < rs) lo = mid; else hi = mid;
     }
-    return 0.5 * (lo + hi);
+    return exp(0.5 * (lo + hi));
+}
+
+double orc_r_of_rstar(double rs, double M, double a) {
+    return horizon_r(M, a) + orc_x_of_rstar(rs, M, a);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -113,11 +127,12 @@ double orc_r_of_rstar(double rs, double M, double a) {
 /* in place of C (Bt, Ath, Bth unchanged: there is no t-r* cross term).      */
 /* out = {b, Re K, Im K, Re Bt, Im Bt, Re C, Im C, Ath, Bth, c}, c = b.      */
 /* ------------------------------------------------------------------------ */
-void orc_coeff_point(double r, double th, double M, double a, int s, int m,
-                     int field, double out[10]) {
+/* x = r - r_+ given beside r (Delta = x (x + r_+ - r_-), no cancellation). */
+static void coeff_point_rx(double r, double x, double th, double M, double a, int s,
+                           int m, int field, double out[10]) {
     double sn = sin(th), cs = cos(th);
     double varpi = r * r + a * a;
-    double Delta = r * r - 2.0 * M * r + a * a;
+    double Delta = x * (x + 2.0 * sqrt(fmax(M * M - a * a, 0.0)));
     double Sigma2 = varpi * varpi - a * a * Delta * sn * sn;
     double Sigma = sqrt(Sigma2);
 
@@ -134,8 +149,8 @@ void orc_coeff_point(double r, double th, double M, double a, int s, int m,
     double Axx = varpi * varpi / Sigma2;
 
     if (field == 1) {
-        /* g1(r) = -N/varpi, N = 2s(r-M) + Delta/r = 2s(r-M) + r - 2M + a^2/r */
-        double N = 2.0 * s * (r - M) + r - 2.0 * M + a * a / r;
+        /* g1(r) = -N/varpi, N = 2s(r-M) + Delta/r */
+        double N = 2.0 * s * (r - M) + Delta / r;
         double dN = 2.0 * s + 1.0 - a * a / (r * r);
         double g1 = -N / varpi;
         double dg1_dr = -(dN * varpi - N * 2.0 * r) / (varpi * varpi);
@@ -156,6 +171,11 @@ void orc_coeff_point(double r, double th, double M, double a, int s, int m,
     out[5] = creal(C);  out[6] = cimag(C);
     out[7] = Ath;       out[8] = Bth;
     out[9] = b;
+}
+
+void orc_coeff_point(double r, double th, double M, double a, int s, int m,
+                     int field, double out[10]) {
+    coeff_point_rx(r, r - horizon_r(M, a), th, M, a, s, m, field, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -258,14 +278,15 @@ void orc_coefficients(const orc_grid* g, double* coef) {
     long plane = (long)nr * nth;
     for (int i = 0; i < nr; ++i) {
         double x = g->rs_min + i * h;
-        double r = (g->coords == 1) ? 0.0 : orc_r_of_rstar(x, g->M, g->a);
+        double xp = (g->coords == 1) ? 0.0 : orc_x_of_rstar(x, g->M, g->a);   /* r - r_+ */
+        double r = horizon_r(g->M, g->a) + xp;
         for (int j = 0; j < nth; ++j) {
             double th = (j + 0.5) * M_PI / nth;
             double c[10];
             if (g->coords == 1)
                 orc_coeff_point_hyp(x, th, g->M, g->a, g->S, g->s, g->m, c);
             else
-                orc_coeff_point(r, th, g->M, g->a, g->s, g->m, g->field, c);
+                coeff_point_rx(r, xp, th, g->M, g->a, g->s, g->m, g->field, c);
             for (int k = 0; k < 10; ++k) coef[k * plane + (long)j * nr + i] = c[k];
         }
     }

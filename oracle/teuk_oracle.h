@@ -49,6 +49,7 @@ typedef struct {
 
 double orc_rstar_of_r(double r, double M, double a);
 double orc_r_of_rstar(double rs, double M, double a);
+double orc_x_of_rstar(double rs, double M, double a);   /* r - r_+ at r*      */
 void   orc_coeff_point(double r, double th, double M, double a, int s, int m,
                        int field, double out[10]);
 double orc_rho_of_r(double r, double S);

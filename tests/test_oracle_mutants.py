@@ -32,12 +32,18 @@ ASSEMBLY = PH + "test_assembly_matches_printed_real_matrices"
 MUTANTS = [
     # tortoise coordinate, Sec. 2.2
     ("tortoise: sign of the r_- logarithm",
-     "- (2.0 * M * rm / (rp - rm)) * log((r - rm) / (2.0 * M));",
-     "+ (2.0 * M * rm / (rp - rm)) * log((r - rm) / (2.0 * M));",
+     "- (2.0 * M * rm / (rp - rm)) * log((x + rp - rm) / (2.0 * M));",
+     "+ (2.0 * M * rm / (rp - rm)) * log((x + rp - rm) / (2.0 * M));",
      [P + "test_tortoise_derivative_and_inverse"]),
     ("tortoise: sign of the extremal pole term",
-     "- 2.0 * M * M / (r - M);", "+ 2.0 * M * M / (r - M);",
+     "- 2.0 * M * M * exp(-y);", "+ 2.0 * M * M * exp(-y);",
      [P + "test_tortoise_derivative_and_inverse"]),
+    ("tortoise: r - r_- written r - r_+ in the logarithm",
+     "log((x + rp - rm) / (2.0 * M));", "log(x / (2.0 * M));",
+     [P + "test_tortoise_derivative_and_inverse"]),
+    ("Delta: r - r_- factor written r - r_+",
+     "double Delta = x * (x + 2.0 * sqrt(fmax(M * M - a * a, 0.0)));",
+     "double Delta = x * x;", [SYM]),
     # coefficients in r*, Eq. teuk0
     ("B*: (r - M) written (r + M)", "2.0 * s * (r - M) * varpi) / Sigma2",
      "2.0 * s * (r + M) * varpi) / Sigma2", [SYM]),
@@ -145,12 +151,13 @@ MUTANTS = [
      "2.0 / 5.0 * u4[k] + dt / 6.0 * F4[k];", [P + "test_ssprk104_fourth_order_convergence"]),
     ("SSP-RK(10,4): dt/6 for dt/10 at the end", "+ 3.0 / 50.0 * dt * F4[k] + dt / 10.0 * Fv[k];",
      "+ 3.0 / 50.0 * dt * F4[k] + dt / 6.0 * Fv[k];", [P + "test_ssprk104_fourth_order_convergence"]),
-    ("r(r*): bisection sides swapped", "if (v < rs) lo = mid; else hi = mid;",
-     "if (v < rs) hi = mid; else lo = mid;", [P + "test_tortoise_derivative_and_inverse"]),
+    ("r(r*): bisection sides swapped", "if (rstar_of_lnx(mid, M, a) < rs) lo = mid; else hi = mid;",
+     "if (rstar_of_lnx(mid, M, a) < rs) hi = mid; else lo = mid;",
+     [P + "test_tortoise_derivative_and_inverse"]),
     ("rescaled field: 2 A** g1 written A** g1", "Bstar = Bstar + 2.0 * Axx * g1;",
      "Bstar = Bstar + Axx * g1;", [SYM_PHI]),
-    ("rescaled field: dropped a^2/r in N", "+ r - 2.0 * M + a * a / r;", "+ r - 2.0 * M;",
-     [SYM_PHI]),
+    ("rescaled field: dropped a^2/r in N", "double N = 2.0 * s * (r - M) + Delta / r;",
+     "double N = 2.0 * s * (r - M) + (Delta - a * a) / r;", [SYM_PHI]),
     ("hyperboloidal b in the complex step: rho for rho^2",
      "return rho * rho * delta / E;", "return rho * delta / E;", [SYM_HYP]),
     ("hyperboloidal sigma: sign under the root",

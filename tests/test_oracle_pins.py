@@ -73,6 +73,56 @@ def test_tortoise_schwarzschild_lambert_w():
         assert abs(o.r_of_rstar(rs, 1.0, 0.0) - r_exact) < 1e-12 * r_exact
 
 
+def test_tortoise_inverse_resolves_r_minus_r_plus_near_the_horizon():
+    """Towards the horizon r - r_+ falls off exponentially in r* (Sec. 2.2's
+    tortoise relation), below the spacing of binary64 numbers near r_+ by
+    r* ~ -70 M at a = 0; the oracle inverts for r - r_+ itself. At a = 0 it is
+    2 W(exp(r*/2M - 1)) (Lambert W); for a = 0.7 M and a = M the forward map,
+    evaluated at 50 digits at the returned r - r_+, must give r* back."""
+    from scipy.special import lambertw
+    for rs in [-70.0, -300.0, -1400.0]:
+        exact = 2.0 * lambertw(np.exp(rs / 2.0 - 1.0)).real
+        assert abs(o.x_of_rstar(rs, 1.0, 0.0) / exact - 1.0) < 1e-12, rs
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    for a in (0.7, 1.0):
+        rp = 1.0 + np.sqrt(1.0 - a * a)
+        for rs in [-40.0, -200.0, -600.0]:
+            x = mp.mpf(o.x_of_rstar(rs, 1.0, a))
+            if a < 1.0:
+                d = mp.sqrt(1 - mp.mpf(a) ** 2)
+                mrp, mrm = 1 + d, 1 - d
+                back = (mrp + x + (2 * mrp / (mrp - mrm)) * mp.log(x / 2)
+                        - (2 * mrm / (mrp - mrm)) * mp.log((x + mrp - mrm) / 2))
+            else:
+                back = 1 + x + 2 * mp.log(x) - 2 / x
+            assert abs(float(back) - rs) < 1e-12 * abs(rs), (a, rs, float(back))
+        assert o.r_of_rstar(-40.0, 1.0, a) == rp + o.x_of_rstar(-40.0, 1.0, a)
+
+
+def test_coefficients_near_the_horizon_keep_their_relative_accuracy():
+    """Delta = (r - r_+)(r - r_-) formed from r - r_+: A^thth = Delta/Sigma^2
+    and Im C (s m a term aside, proportional to Delta) at r* = -70 M agree
+    with a 50-digit evaluation at the same r - r_+ to 1e-13 relative."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    for a, s, m in [(0.0, 0, 0), (0.5, -1, 0), (0.999, -2, 2)]:
+        g = o.grid(7, 5, -70.0, -64.0, 1.0, a, s, m)
+        co = o.coefficients(g)
+        ma = mp.mpf(a)
+        d = mp.sqrt(1 - ma ** 2)
+        for i in range(7):
+            x = mp.mpf(o.x_of_rstar(-70.0 + i, 1.0, a))
+            r = 1 + d + x
+            Delta = x * (x + 2 * d)
+            for j in range(5):
+                th = mp.mpf((j + 0.5) * np.pi / 5)
+                varpi = r * r + ma ** 2
+                Sigma2 = varpi ** 2 - ma ** 2 * Delta * mp.sin(th) ** 2
+                ath = Delta / Sigma2
+                assert abs(co[7, j, i] / float(ath) - 1.0) < 1e-13, (a, i, j)
+
+
 # --------------------------------------------------------------------------
 # WENO5 (Sec. 3.1.2)
 # --------------------------------------------------------------------------
