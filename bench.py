@@ -43,13 +43,20 @@ FP64_FLOPS_PER_PT_STAGE = 112.0
 # (32 B), u_out (32 B), u^n in stages 2 and 3 (2/3 x 32 B).
 BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # DRAM bytes (read + write) per launch of the binary32-weight stage kernel,
-# averaged over the three stages, from one ncu capture of this workload
-# (profiles/stage_kernel_kerr2048x128.md); valid only for the kernel sources it
-# was taken on, identified by the sha256 of their concatenation.
+# averaged over the three stages, from one ncu capture of this workload on
+# these kernel sources; valid only for the sources it was taken on, identified
+# by the sha256 of their concatenation.
 NCU_TRAFFIC = {"sources": ["paper_2010_04760_gb300/csrc/teuk_stage_kernels.cuh",
                            "paper_2010_04760_gb300/csrc/teuk_stage.cu"],
                "sha256": "c32d877859ddf5d6692fcc9053d184f524b8287fad2f7fa28bf4d6d877cde37c",
-               "bytes_per_launch": (31478272 + 39867392 + 39868416) / 3.0}
+               "bytes_per_launch": (31478272 + 39867392 + 39868416) / 3.0,
+               "fused_bytes_per_launch": None}
+
+
+def workload_config(wl, wprec):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": wl.name, "nr": wl.nr, "ntheta": wl.nth, "a": wl.a, "s": wl.s,
+            "m": wl.m, "wprec": wprec, "rk": "SSP-RK(3,3)"}
 
 
 def kernel_source_digest(sources=None):
@@ -61,12 +68,14 @@ def kernel_source_digest(sources=None):
     return h.hexdigest()
 
 
-def ncu_traffic():
+def ncu_traffic(fused=False):
     try:
         digest = kernel_source_digest()
     except OSError:
         return None
-    return NCU_TRAFFIC["bytes_per_launch"] if digest == NCU_TRAFFIC["sha256"] else None
+    if digest != NCU_TRAFFIC["sha256"]:
+        return None
+    return NCU_TRAFFIC["fused_bytes_per_launch" if fused else "bytes_per_launch"]
 
 
 # Binary64 FMA lanes per SM per clock on GB300 (its nominal 1.26 TFLOP/s =
@@ -166,10 +175,14 @@ def barrier(world):
         dist.barrier()
 
 
-def time_gpu_steps(T, torch, wprec, steps, warmup, stream, flush):
-    """Device time of `steps` RK steps of the workload with weights `wprec`."""
+def time_gpu_steps(T, torch, wprec, steps, warmup, stream, flush, launch=None):
+    """Device time of `steps` RK steps of the workload with weights `wprec`
+    (launch: a teuk_launch mode, default the library's choice)."""
     p = T.params_from_workload(WL, wprec=wprec)
     h = T.teuk_create(p, stream)
+    if launch is not None:
+        T.teuk_set_launch(h, launch)
+    time_gpu_steps.launch_used = "fused" if T.teuk_get_launch(h)[2] == 1 else "stages"
     T.teuk_set_state(h, I.initial_data(WL), 0.0)
     for _ in range(warmup):
         T.teuk_step(h, 1)
@@ -191,9 +204,10 @@ def time_gpu_steps(T, torch, wprec, steps, warmup, stream, flush):
     return sum(ms), ms
 
 
-def waveform_error(T, torch, stream, t_end=150.0, r_ext=50.0):
+def waveform_error(T, torch, stream, t_end=WL.t_end, r_ext=50.0):
     """Relative L2 difference of the waveform (Psi at r* = r_ext over all theta,
-    sampled every 100 steps up to t_end) between binary32 and binary64 weights."""
+    sampled every 100 steps up to t_end, the workload's stated duration of
+    500 M) between binary32 and binary64 weights."""
     waves = {}
     t = 0.0
     for wprec in ("fp64", "fp32"):
@@ -211,13 +225,64 @@ def waveform_error(T, torch, stream, t_end=150.0, r_ext=50.0):
     return float(err), t
 
 
-def time_e2e(T, torch, steps, stream, lanes=3):
-    """Same metric through the public handle API with host buffers: every step
-    copies its input state in from pinned host memory, advances one RK step
-    and reads its result back to pinned host memory. The steps are
-    independent problems (each starts from the same input), spread over
-    `lanes` handles on their own streams with the asynchronous copy calls, so
-    one problem's copies overlap another's stepping."""
+def time_multi_step(T, torch, wprec, steps, warmup, stream, flush):
+    """Device time of `steps` RK steps issued as one teuk_step call (the way a
+    long evolution runs), L2 flushed before the call."""
+    p = T.params_from_workload(WL, wprec=wprec)
+    h = T.teuk_create(p, stream)
+    T.teuk_set_state(h, I.initial_data(WL), 0.0)
+    T.teuk_step(h, max(warmup, 4))
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.fill_(1)
+        e0.record(stream)
+        T.teuk_step(h, steps)
+        e1.record(stream)
+    stream.synchronize()
+    assert T.teuk_check_finite(h) == T.TEUK_OK
+    h.close()
+    return e0.elapsed_time(e1)
+
+
+def time_e2e(T, torch, steps, warmup, stream, flush):
+    """The metric end to end through the public handle API with host buffers,
+    timed like the device value: one handle on the bench stream, L2 flushed
+    before every step (outside the timed region), and per step CUDA events
+    around the upload of the step's input state from pinned host memory
+    (teuk_set_state_async), one RK step (teuk_step) and the read-back of its
+    result into pinned host memory (teuk_get_state_async)."""
+    p = T.params_from_workload(WL)
+    h = T.teuk_create(p, stream)
+    src = torch.empty((4, WL.nth, WL.nr), dtype=torch.float64, pin_memory=True).numpy()
+    src[...] = I.initial_data(WL)
+    dst = torch.empty((4, WL.nth, WL.nr), dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(warmup):
+        T.teuk_set_state_async(h, src, 0.0)
+        T.teuk_step(h, 1)
+        T.teuk_get_state_async(h, dst)
+    T.teuk_synchronize(h)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            T.teuk_set_state_async(h, src, 0.0)
+            T.teuk_step(h, 1)
+            T.teuk_get_state_async(h, dst)
+            ev[k][1].record(stream)
+    T.teuk_synchronize(h)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ok = bool(np.isfinite(dst).all())
+    h.close()
+    return ms, src.nbytes, ok
+
+
+def time_e2e_pipelined(T, torch, steps, lanes=3):
+    """Independent problems pipelined over `lanes` handles, each on its own
+    stream: one problem's copies overlap another's stepping, and the streams'
+    kernels may run concurrently; no L2 flush. Wall-clock seconds."""
     p = T.params_from_workload(WL)
     hs = [T.teuk_create(p) for _ in range(lanes)]
     ins, outs = [], []
@@ -242,11 +307,41 @@ def time_e2e(T, torch, steps, stream, lanes=3):
     t0 = time.perf_counter()
     run(steps)
     el = time.perf_counter() - t0
-    ok = all(np.isfinite(o).all() for o in outs)
     for h in hs:
         h.close()
-    nbytes = ins[0].nbytes
-    return el, nbytes, ok
+    return el
+
+
+def time_workload(T, torch, wl, wprec, steps, warmup, stream, flush, fp64_peak_derived):
+    """Device time per RK step of workload wl with weights wprec (L2 flushed
+    before every step), its throughput and its binary64-pipe fraction."""
+    p = T.params_from_workload(wl, wprec=wprec)
+    h = T.teuk_create(p, stream)
+    T.teuk_set_state(h, I.initial_data(wl), 0.0)
+    for _ in range(warmup):
+        T.teuk_step(h, 1)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            T.teuk_step(h, 1)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    finite = T.teuk_check_finite(h) == T.TEUK_OK
+    h.close()
+    pts = wl.nr * wl.nth
+    rate = pts * 3 / (ms * 1e-3)
+    out = {"value": rate, "unit": UNIT, "ms_per_step": ms, "steps": steps, "finite": finite}
+    if wprec != "fp64":
+        tf = FP64_FLOPS_PER_PT_STAGE * rate / 1e12
+        out["fp64_tflops"] = tf
+        out["fp64_frac"] = tf / fp64_peak_derived
+        out["hbm_gbs"] = BYTES_PER_PT_STAGE * rate / 1e9
+    return out
 
 
 def time_batch(T, torch, stream, steps=32):
@@ -336,7 +431,9 @@ def run_reference(args, rank, world):
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "weights_dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WL.name, "nr": WL.nr, "ntheta": WL.nth, "wprec": "fp32"},
+            "config": {**workload_config(WL, "fp32"),
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas x1"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} RK steps of the {WL.nr}x{WL.nth} workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -366,19 +463,35 @@ def main():
     stream = torch.cuda.Stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
-    # binary64-weight baseline on the same workload
-    barrier(world)
-    ms64, _ = time_gpu_steps(T, torch, "fp64", args.steps, args.warmup, stream, flush)
-    ms64 = max_over_ranks(ms64, world, device)
-    # mixed precision (binary32 weights): the headline
-    barrier(world)
+    # clocks sampled over every device-timed region of the workload (the
+    # binary64-weight baseline, the headline, the stage-launch comparison and
+    # the end-to-end run)
     with ClockSampler(local) as clk:
+        # binary64-weight baseline on the same workload
+        barrier(world)
+        ms64, _ = time_gpu_steps(T, torch, "fp64", args.steps, args.warmup, stream, flush)
+        ms64 = max_over_ranks(ms64, world, device)
+        # mixed precision (binary32 weights): the headline
+        barrier(world)
         ms32, per = time_gpu_steps(T, torch, "fp32", args.steps, args.warmup, stream, flush)
-    ms32 = max_over_ranks(ms32, world, device)
-    barrier(world)
-    e2e_steps = max(60, args.steps)
-    e2e_s, nbytes, e2e_ok = time_e2e(T, torch, e2e_steps, stream)
-    e2e_s = max_over_ranks(e2e_s, world, device)
+        ms32 = max_over_ranks(ms32, world, device)
+        launch32 = time_gpu_steps.launch_used
+        # the same, one step per call, with the other schedule
+        other_launch = T.TEUK_LAUNCH_FUSED if launch32 == "stages" else T.TEUK_LAUNCH_STAGES
+        barrier(world)
+        ms32s, _ = time_gpu_steps(T, torch, "fp32", args.steps, args.warmup, stream, flush,
+                                  other_launch)
+        ms32s = max_over_ranks(ms32s, world, device)
+        # all K steps in one teuk_step call (the fused step: one persistent
+        # launch), L2 flushed once before
+        barrier(world)
+        ms32m = time_multi_step(T, torch, "fp32", args.steps, args.warmup, stream, flush)
+        ms32m = max_over_ranks(ms32m, world, device)
+        barrier(world)
+        e2e_ms, nbytes, e2e_ok = time_e2e(T, torch, args.steps, args.warmup, stream, flush)
+        e2e_ms = max_over_ranks(e2e_ms, world, device)
+    pipe_steps = max(60, args.steps)
+    pipe_s = max_over_ranks(time_e2e_pipelined(T, torch, pipe_steps), world, device)
     err, t_err = waveform_error(T, torch, stream) if rank == 0 else (None, None)
     batch = time_batch(T, torch, stream) if rank == 0 else None
     paper_run = time_paper_run(T, torch, stream) if rank == 0 else None
@@ -390,22 +503,46 @@ def main():
     fp64_peak_derived = SMS * FP64_FMA_LANES_PER_SM_CLK * 2 * sm_clock_mhz * 1e6 / 1e12
     value = weak_scaling_value(POINTS * 3, args.steps, world, ms32)
     value64 = weak_scaling_value(POINTS * 3, args.steps, world, ms64)
-    launch_ms = ms32 / (3 * args.steps)
+    fused = launch32 == "fused"
+    launch_ms = ms32 / (3 * args.steps)          # per stage
     achieved_tf = FP64_FLOPS_PER_PT_STAGE * POINTS / (launch_ms * 1e-3) / 1e12
     achieved_gbs = BYTES_PER_PT_STAGE * POINTS / (launch_ms * 1e-3) / 1e9
     peaks = load_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     if rank != 0:
         return
+    # the other large workloads: the extremal scalar 8192 x 256 with binary16
+    # and bfloat16 weights, the tail workload 16384 x 512 with binary32, each
+    # beside binary64 weights (device-timed per step, L2 flushed as above)
+    other = {}
+    for wl, formats in ((I.EXTREMAL_SCALAR, ("fp64", "fp16", "bf16")),
+                        (I.TAIL_SCALAR, ("fp64", "fp32"))):
+        rows = {w: time_workload(T, torch, wl, w, 10, 3, stream, flush, fp64_peak_derived)
+                for w in formats}
+        for w in formats[1:]:
+            rows[w]["speedup_vs_fp64_weights"] = rows[w]["value"] / rows["fp64"]["value"]
+        other[wl.name] = {"config": workload_config(wl, formats[1]), **rows}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "weights_dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WL.name, "nr": WL.nr, "ntheta": WL.nth, "a": WL.a, "s": WL.s,
-                   "m": WL.m, "wprec": "fp32", "rk": "SSP-RK(3,3)",
+        "config": {**workload_config(WL, "fp32"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
+        "launch": ("fused step (one persistent launch per step)" if fused
+                   else "three stage launches per step (programmatic dependent launch)"),
+        "other_launch_per_step": {
+            "value": weak_scaling_value(POINTS * 3, args.steps, world, ms32s),
+            "ms_per_step": ms32s / args.steps,
+            "how": ("the same, one step per call, as " +
+                    ("three stage launches" if fused else "one fused persistent launch"))},
+        "one_call_of_k_steps": {
+            "value": weak_scaling_value(POINTS * 3, args.steps, world, ms32m),
+            "ms_per_step": ms32m / args.steps,
+            "how": f"the same {args.steps} steps as one teuk_step call: one fused persistent "
+                   "launch (up to 1024 steps), L2 flushed once before; how a long evolution "
+                   "runs (the state stays L2-resident between steps)"},
         "fp64_weights": {"value": value64, "ms_per_step": ms64 / args.steps},
         "mixed_speedup_vs_fp64_weights": value / value64,
         "paper_mixed_speedup_context": {
@@ -416,8 +553,9 @@ def main():
         "waveform_error_window": f"Psi(r*=50M, all theta) every 100 steps to t={t_err:.1f}M",
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_derived,
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak_derived,
-                     "traffic": ncu_traffic(), "traffic_unit": "bytes per launch",
-                     "algorithmic_bytes_per_launch": BYTES_PER_PT_STAGE * POINTS,
+                     "traffic": ncu_traffic(fused), "traffic_unit": "bytes per launch",
+                     "algorithmic_bytes_per_launch":
+                         BYTES_PER_PT_STAGE * POINTS * (3 if fused else 1),
                      "pipe": "fp64",
                      "peak_source": f"derived: {SMS} SMs x {FP64_FMA_LANES_PER_SM_CLK} binary64 "
                                     f"FMA lanes/clk x 2 flops x {sm_clock_mhz:.0f} MHz "
@@ -426,21 +564,29 @@ def main():
                      "frac_of_measured_sustained": achieved_tf / fp64_peak_tf,
                      "measured_source": "teuk_fp64_fma_rate: independent binary64 FMA "
                                         "chains on this GPU, x2 flops",
-                     "kernel": "stage_kernel<fp32 weights>",
+                     "kernel": ("fused_step_kernel<fp32 weights> (one launch = one step "
+                                "= 3 stages)") if fused else "stage_kernel<fp32 weights>",
                      "flops_per_point_stage": FP64_FLOPS_PER_PT_STAGE},
         "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak,
                          "bytes_per_point_stage": BYTES_PER_PT_STAGE},
-        "e2e": {"value": POINTS * 3 * e2e_steps * world / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                "steps": e2e_steps, "lanes": 3, "finite": e2e_ok,
-                "how": "per step: pinned host -> device state, one RK step, device -> pinned "
-                       "host result; independent steps on 3 handles/streams (async copies), "
-                       "whose kernels may overlap; no L2 flush (the device-timed value "
-                       "flushes L2 before every step and runs one evolution serially)"},
+        "e2e": {"value": weak_scaling_value(POINTS * 3, args.steps, world, e2e_ms),
+                "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": args.steps, "ms_per_step": e2e_ms / args.steps, "finite": e2e_ok,
+                "how": "per step, timed with CUDA events on one handle's stream after an L2 "
+                       "flush: teuk_set_state_async from pinned host memory, teuk_step(1), "
+                       "teuk_get_state_async to pinned host memory (the device value's step "
+                       "plus both copies)"},
+        "e2e_pipelined_3_handles": {
+            "value": POINTS * 3 * pipe_steps * world / pipe_s, "unit": UNIT,
+            "steps": pipe_steps, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "how": "independent steps over 3 handles on 3 streams with the asynchronous copy "
+                   "calls (one problem's copies overlap another's step, kernels of different "
+                   "streams may run concurrently), wall clock, no L2 flush"},
+        "other_workloads": other,
         "batched_64_uneven_evolutions": batch,
         "paper_run_hyperboloidal_16384x64": paper_run,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (1 if fused else 3) * args.steps,
         "clocks": clk.summary(),
     }
     v, n, el, cores = oracle_rate()

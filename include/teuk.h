@@ -52,7 +52,7 @@ typedef enum {
     TEUK_ERR_ARG = 1,        /* invalid argument (message via teuk_last_error) */
     TEUK_ERR_CUDA = 2,       /* a CUDA call failed                               */
     TEUK_ERR_NONFINITE = 3,  /* the state holds a NaN or an infinity             */
-    TEUK_ERR_TIMEOUT = 4,    /* reserved: no kernel of this library waits        */
+    TEUK_ERR_TIMEOUT = 4,    /* a device-side wait of the fused step ran out     */
     TEUK_ERR_STATE = 5,      /* reserved: no call depends on an earlier one      */
     TEUK_ERR_HOST = 6        /* host memory or a host thread was not available   */
 } teuk_status;
@@ -113,6 +113,16 @@ typedef enum {
                                       Both radial schemes and both theta
                                       modes; batches too.                     */
 } teuk_coords;
+
+/* How teuk_step launches a step (see teuk_set_launch). */
+typedef enum {
+    TEUK_LAUNCH_AUTO = 0,     /* the fused step for calls of >= 4 steps on grids
+                                 with at least as many work items per stage as
+                                 the device holds blocks, else stages           */
+    TEUK_LAUNCH_STAGES = 1,   /* one launch per Runge-Kutta stage (CUDA graph)  */
+    TEUK_LAUNCH_FUSED = 2     /* one persistent launch for all stages of up to
+                                 1024 steps (SSP-RK(3,3) with WENO5 only)       */
+} teuk_launch;
 
 /* Evolved field. */
 typedef enum {
@@ -191,8 +201,9 @@ size_t teuk_coeff_count(const teuk_params* p);
 /* Kernel coefficient array for time step dt, written to host memory
  * coef_host[teuk_coeff_count(p)]. The planes are the first-order matrices
  * M, A, L of Sec. 2.3 pre-multiplied by the forward-Euler stage step of p's
- * integrator (dt for SSP-RK(3,3), dt/6 for SSP-RK(10,4)) and by 1/(6h),
- * 1/(12 dtheta^k) for the stencil normalisations, with the theta pole parity
+ * integrator (dt for SSP-RK(3,3), dt/6 for SSP-RK(10,4)) and by 1/(6h)
+ * (1/(60h) with TEUK_SCHEME_FD6_KO8), 1/(12 dtheta^k) for the stencil
+ * normalisations, with the theta pole parity
  * folded into the theta-stencil planes. Built on the host in binary64; r(r*)
  * from the tortoise relation of Sec. 2.2; on the hyperboloidal slices the
  * coefficients of Eq. near_final for Phi, derived from Eq. teuk0 (they are
@@ -314,10 +325,45 @@ teuk_status teuk_get_state_async(teuk_handle* h, double* u_host);
 /* Wait until everything enqueued on the handle's stream has completed. */
 teuk_status teuk_synchronize(teuk_handle* h);
 
-/* Advance nsteps steps of p's integrator (3 fused stage launches each for
- * SSP-RK(3,3), 11 for SSP-RK(10,4)), replayed from a captured CUDA graph.
- * Asynchronous on the handle's stream. */
+/* Advance nsteps steps of p's integrator. With the fused step (by default
+ * for SSP-RK(3,3) with WENO5 when nsteps >= 4 and the grid has at least as
+ * many work items per stage as resident blocks; see teuk_set_launch) one
+ * persistent launch runs
+ * every stage of up to 1024 steps: work items (4 theta rows x one radial
+ * segment) are taken in stage order, and an item starts as soon as the eight
+ * items around it have finished the previous stage, so stages overlap
+ * instead of ending at a launch boundary. Otherwise 3 fused stage launches
+ * per step for SSP-RK(3,3), 11 for SSP-RK(10,4), replayed from a captured CUDA
+ * graph. Both give bitwise the same state. Asynchronous on the handle's
+ * stream. Returns TEUK_ERR_TIMEOUT, without launching, if an earlier fused
+ * launch of h ran out of a device-side wait. */
 teuk_status teuk_step(teuk_handle* h, int64_t nsteps);
+
+/* Launch mode of teuk_step (teuk_launch) and the bound of each device-side
+ * wait of the fused step in seconds, wait_seconds in [1e-6, 3600] (default 2:
+ * a wait lasts about one work item, tens of microseconds, when all is well).
+ * A wait that runs out makes every block of the launch stop; the next call
+ * that synchronises the handle's stream (teuk_synchronize, teuk_observe,
+ * teuk_get_state, teuk_set_state, teuk_check_finite) or the next teuk_step
+ * returns TEUK_ERR_TIMEOUT, and the state is then undefined (restore it with
+ * teuk_set_state). TEUK_LAUNCH_FUSED needs SSP-RK(3,3) with the WENO5 scheme
+ * (TEUK_ERR_ARG otherwise). The paper has no counterpart: this is how the
+ * library schedules its kernels. */
+teuk_status teuk_set_launch(teuk_handle* h, int mode, double wait_seconds);
+
+/* The launch mode set by teuk_set_launch (TEUK_LAUNCH_AUTO unless changed),
+ * the wait bound, and the smallest nsteps for which teuk_step uses the fused
+ * step (1, 4, or 0 for never). Any output may be NULL. */
+teuk_status teuk_get_launch(const teuk_handle* h, int* mode_out, double* wait_seconds_out,
+                            int64_t* fused_from_steps_out);
+
+/* Test hook for the timeout path (no counterpart in the paper): the next
+ * fused launch of h does not publish the completion of its first work item's
+ * first stage, a flag nothing else sets, so the waits that depend on it run
+ * out after the wait bound and the launch ends early with the state
+ * undefined; the next synchronising call returns TEUK_ERR_TIMEOUT.
+ * TEUK_ERR_ARG unless the handle's launch mode is TEUK_LAUNCH_FUSED. */
+teuk_status teuk_test_withhold(teuk_handle* h);
 
 /* Observation (Sec. 4): wave[2*ntheta] = Psi (re, im) along theta at the
  * radial node nearest rstar_ext (an r* or a rho: rho = S reads the field at

@@ -26,6 +26,7 @@ TEUK_RK_SSP33, TEUK_RK_SSP104 = 0, 1
 TEUK_SCHEME_WENO5, TEUK_SCHEME_FD6_KO8 = 0, 1
 TEUK_COORDS_RSTAR, TEUK_COORDS_HYPERBOLOIDAL = 0, 1
 TEUK_FIELD_PSI, TEUK_FIELD_PHI = 0, 1
+TEUK_LAUNCH_AUTO, TEUK_LAUNCH_STAGES, TEUK_LAUNCH_FUSED = 0, 1, 2
 WPREC = {"fp64": TEUK_W_FP64, "fp32": TEUK_W_FP32, "fp16": TEUK_W_FP16, "bf16": TEUK_W_BF16}
 
 
@@ -87,6 +88,9 @@ def lib():
             "teuk_observe": (I, [P, D, P, P, P]),
             "teuk_check_finite": (I, [P]),
             "teuk_state_dev": (I, [P, P]),
+            "teuk_set_launch": (I, [P, I, D]),
+            "teuk_get_launch": (I, [P, P, P, P]),
+            "teuk_test_withhold": (I, [P]),
             "teuk_batch_create": (I, [PP, I, P, I, P]),
             "teuk_batch_destroy": (I, [P]),
             "teuk_batch_set_state": (I, [P, I, P, D]),
@@ -379,6 +383,22 @@ def teuk_observe(h, rstar_ext):
 
 def teuk_check_finite(h):
     return lib().teuk_check_finite(h.ptr)
+
+
+def teuk_set_launch(h, mode, wait_seconds=2.0):
+    _check(lib().teuk_set_launch(h.ptr, int(mode), float(wait_seconds)))
+
+
+def teuk_get_launch(h):
+    """(mode, wait_seconds, smallest nsteps run by the fused step or 0)."""
+    mode, wait, k = ctypes.c_int(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().teuk_get_launch(h.ptr, ctypes.byref(mode), ctypes.byref(wait),
+                                 ctypes.byref(k)))
+    return mode.value, wait.value, k.value
+
+
+def teuk_test_withhold(h):
+    _check(lib().teuk_test_withhold(h.ptr))
 
 
 def teuk_state_dev(h):

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libteuk.so")
-SOURCES = ["teuk_host.cpp", "teuk_stage.cu", "teuk_stage_hyp.cu", "teuk_api.cu"]
+SOURCES = ["teuk_host.cpp", "teuk_stage.cu", "teuk_stage_hyp.cu", "teuk_fused.cu",
+           "teuk_fused_hyp.cu", "teuk_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

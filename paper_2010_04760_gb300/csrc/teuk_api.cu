@@ -161,8 +161,44 @@ struct teuk_handle {
     int* flag = nullptr;
     cudaGraphExec_t exec = nullptr;
     int chunk = 0;
+    // fused step kernel (SSP-RK(3,3) with WENO5): completion flags per work
+    // item, control block, host-mapped error words {code, epoch, item}
+    unsigned* fflags = nullptr;
+    void* fctl = nullptr;
+    int* err_host = nullptr;
+    int* err_dev = nullptr;
+    int launch = TEUK_LAUNCH_AUTO;
+    double wait_s = 2.0;
+    int withhold = 0;
+    long long fused_items = 0, fused_blocks = 0;   // work items per stage, resident blocks
     size_t plane() const { return (size_t)p.nr * p.ntheta; }
+    bool fused_ok() const { return p.rk == TEUK_RK_SSP33 && p.scheme == TEUK_SCHEME_WENO5; }
+    // The schedule of a teuk_step call of nsteps steps. AUTO: the fused step
+    // for calls of at least kFusedMinSteps steps on grids with at least as
+    // many work items per stage as resident blocks; otherwise stage launches
+    // (a single step has too few stages to amortise the persistent launch's
+    // ramp and tail, and a smaller grid leaves blocks waiting on each other).
+    static constexpr int64_t kFusedMinSteps = 4;
+    int launch_for(int64_t nsteps) const {
+        if (launch == TEUK_LAUNCH_STAGES || !fused_ok()) return TEUK_LAUNCH_STAGES;
+        if (launch == TEUK_LAUNCH_FUSED) return TEUK_LAUNCH_FUSED;
+        return (nsteps >= kFusedMinSteps && fused_items >= fused_blocks) ? TEUK_LAUNCH_FUSED
+                                                                        : TEUK_LAUNCH_STAGES;
+    }
 };
+
+// TEUK_ERR_TIMEOUT if a fused launch of h ran out of a device-side wait (read
+// after the stream has passed it); clears the record.
+static teuk_status wait_status(teuk_handle* h) {
+    volatile int* eh = h->err_host;
+    if (!eh || eh[0] == 0) return TEUK_OK;
+    const int epoch = eh[1], item = eh[2];
+    eh[0] = 0;
+    return fail(TEUK_ERR_TIMEOUT, "a device-side wait of the fused step ran out (stage " +
+                                      std::to_string(epoch % 3 + 1) + " of step " +
+                                      std::to_string(epoch / 3) + " of the launch, work item " +
+                                      std::to_string(item) + "); the state is undefined");
+}
 
 extern "C" {
 
@@ -504,6 +540,9 @@ teuk_status teuk_destroy(teuk_handle* h) {
     cudaFree(h->coef);
     cudaFree(h->obs);
     cudaFree(h->flag);
+    cudaFree(h->fflags);
+    cudaFree(h->fctl);
+    if (h->err_host) cudaFreeHost(h->err_host);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return TEUK_OK;
@@ -538,6 +577,24 @@ teuk_status teuk_create(const teuk_params* p, void* stream, teuk_handle** out) {
         if (e == cudaSuccess) e = cudaMalloc(&h->coef, coef.size() * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&h->obs, 8 * (size_t)p->ntheta * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
+        if (e == cudaSuccess && h->fused_ok()) {
+            h->fused_items = (long long)fused_items(h->p);
+            e = fused_resident_blocks(h->p, &h->fused_blocks);
+        }
+        if (e == cudaSuccess && h->fused_ok()) {
+            const size_t nf = fused_items(h->p) * sizeof(unsigned);
+            e = cudaMalloc(&h->fflags, nf);
+            if (e == cudaSuccess) e = cudaMalloc(&h->fctl, fused_ctl_bytes());
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->fflags, 0, nf, h->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->fctl, 0, fused_ctl_bytes(), h->stream);
+            if (e == cudaSuccess)
+                e = cudaHostAlloc(reinterpret_cast<void**>(&h->err_host), 3 * sizeof(int),
+                                  cudaHostAllocMapped);
+            if (e == cudaSuccess) {
+                h->err_host[0] = h->err_host[1] = h->err_host[2] = 0;
+                e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->err_dev), h->err_host, 0);
+            }
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, 4 * n * sizeof(double), h->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h->coef, coef.data(), coef.size() * sizeof(double),
@@ -571,6 +628,8 @@ teuk_status teuk_set_state(teuk_handle* h, const double* u_host, double t) {
                                   cudaMemcpyHostToDevice, h->stream));
         TEUK_CUDA(cudaStreamSynchronize(h->stream));
         h->t = t;
+        teuk_status ws = wait_status(h);
+        if (ws != TEUK_OK) return ws;
         clear_error();
         return TEUK_OK;
     });
@@ -583,6 +642,8 @@ teuk_status teuk_get_state(teuk_handle* h, double* u_host, double* t_out) {
                                   cudaMemcpyDeviceToHost, h->stream));
         TEUK_CUDA(cudaStreamSynchronize(h->stream));
         if (t_out) *t_out = h->t;
+        teuk_status ws = wait_status(h);
+        if (ws != TEUK_OK) return ws;
         clear_error();
         return TEUK_OK;
     });
@@ -613,6 +674,8 @@ teuk_status teuk_synchronize(teuk_handle* h) {
     return guarded("teuk_synchronize", [&]() -> teuk_status {
         if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
         TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        teuk_status ws = wait_status(h);
+        if (ws != TEUK_OK) return ws;
         clear_error();
         return TEUK_OK;
     });
@@ -687,6 +750,23 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
         NvtxRange trace("teuk_step");
         if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
         if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
+        teuk_status ws = wait_status(h);          // an earlier launch that already ran out
+        if (ws != TEUK_OK) return ws;
+        if (h->launch_for(nsteps) == TEUK_LAUNCH_FUSED) {
+            // one launch per 1024 steps (bounds a launch's duration)
+            FusedRun run{h->fflags, h->fctl, h->err_dev,
+                         (unsigned long long)(h->wait_s * 1e9), h->withhold, 0};
+            for (int64_t left = nsteps; left > 0;) {
+                const int k = (int)std::min<int64_t>(left, 1024);
+                TEUK_CUDA(launch_fused_step(h->p, h->coef, h->dt, h->u, h->w, k, run, h->stream));
+                run.withhold = 0;
+                h->withhold = 0;
+                left -= k;
+            }
+            h->t += (double)nsteps * h->dt;
+            clear_error();
+            return TEUK_OK;
+        }
         const int kChunk = 16;
         if (nsteps >= kChunk && !h->exec) {
             cudaGraph_t g = nullptr;
@@ -735,6 +815,8 @@ teuk_status teuk_observe(teuk_handle* h, double rstar_ext, double* wave, double*
         TEUK_CUDA(cudaMemcpyAsync(o.data(), h->obs, o.size() * sizeof(double),
                                   cudaMemcpyDeviceToHost, h->stream));
         TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        teuk_status ws = wait_status(h);
+        if (ws != TEUK_OK) return ws;
         for (double v : o)
             if (!std::isfinite(v)) return fail(TEUK_ERR_NONFINITE, "observed value is not finite");
         if (wave) std::memcpy(wave, o.data(), 2 * (size_t)nth * sizeof(double));
@@ -754,7 +836,53 @@ teuk_status teuk_check_finite(teuk_handle* h) {
         int flag = 0;
         TEUK_CUDA(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         TEUK_CUDA(cudaStreamSynchronize(h->stream));
+        teuk_status ws = wait_status(h);
+        if (ws != TEUK_OK) return ws;
         if (flag) return fail(TEUK_ERR_NONFINITE, "state holds NaN or infinity");
+        clear_error();
+        return TEUK_OK;
+    });
+}
+
+teuk_status teuk_set_launch(teuk_handle* h, int mode, double wait_seconds) {
+    return guarded("teuk_set_launch", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (mode != TEUK_LAUNCH_AUTO && mode != TEUK_LAUNCH_STAGES && mode != TEUK_LAUNCH_FUSED)
+            return fail(TEUK_ERR_ARG, "unknown launch mode");
+        if (mode == TEUK_LAUNCH_FUSED && !h->fused_ok())
+            return fail(TEUK_ERR_ARG, "the fused step needs SSP-RK(3,3) and the WENO5 scheme");
+        if (!(wait_seconds >= 1e-6 && wait_seconds <= 3600.0))
+            return fail(TEUK_ERR_ARG, "wait_seconds must be in [1e-6, 3600]");
+        h->launch = mode;
+        h->wait_s = wait_seconds;
+        clear_error();
+        return TEUK_OK;
+    });
+}
+
+teuk_status teuk_get_launch(const teuk_handle* h, int* mode_out, double* wait_seconds_out,
+                            int64_t* fused_from_steps_out) {
+    return guarded("teuk_get_launch", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (mode_out) *mode_out = h->launch;
+        if (wait_seconds_out) *wait_seconds_out = h->wait_s;
+        if (fused_from_steps_out) {
+            int64_t k = 0;
+            if (h->launch_for(1) == TEUK_LAUNCH_FUSED) k = 1;
+            else if (h->launch_for(teuk_handle::kFusedMinSteps) == TEUK_LAUNCH_FUSED)
+                k = teuk_handle::kFusedMinSteps;
+            *fused_from_steps_out = k;
+        }
+        return TEUK_OK;
+    });
+}
+
+teuk_status teuk_test_withhold(teuk_handle* h) {
+    return guarded("teuk_test_withhold", [&]() -> teuk_status {
+        if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
+        if (h->launch != TEUK_LAUNCH_FUSED)
+            return fail(TEUK_ERR_ARG, "set TEUK_LAUNCH_FUSED first (teuk_set_launch)");
+        h->withhold = 1;
         clear_error();
         return TEUK_OK;
     });

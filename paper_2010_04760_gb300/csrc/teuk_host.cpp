@@ -425,7 +425,9 @@ teuk_status teuk_build_coefficients(const teuk_params* p, double dt, double* coe
         const double dth = M_PI / nth;
         const double sigma = ((p->m + p->s) % 2 == 0) ? 1.0 : -1.0;   // pole parity
         dt = stage_step(*p, dt);                 // forward-Euler step of one stage
-        const double c6h = dt / (6.0 * h);
+        // radial planes: the WENO5 kernel forms 6 h D, the FD6 + KO8 kernel
+        // 60 h D (the sixth-order stencil's own normalisation)
+        const double c6h = dt / ((p->scheme == TEUK_SCHEME_FD6_KO8 ? 60.0 : 6.0) * h);
         std::vector<double> r, x;
         radial_nodes(*p, r, x);
         for_rows(nth, (long long)nr * nth, [&](int j0, int j1) {

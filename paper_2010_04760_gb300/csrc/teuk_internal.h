@@ -17,7 +17,8 @@ inline int coef_planes(const teuk_params& p) {
     if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) return 13;
     return p.theta_mode == TEUK_THETA_WENO5 ? 12 : kCoefPlanes;
 }
-// Plane order (all pre-multiplied by dt):
+// Plane order (all pre-multiplied by dt; 60h in place of 6h for the FD6 + KO8
+// scheme):
 //   0 cb   = b/(6h)          1 cKr = Re K/(6h)     2 cKi = Im K/(6h)
 //   3 cBr  = Re Bt           4 cBi = Im Bt         5 cCi = Im C
 //   6..10  theta stencil weights on Psi rows j-2, j-1, j, j+1, j+2
@@ -98,5 +99,20 @@ cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_des
 cudaError_t launch_batch_stage(int wprec, int theta, bool hyp, int stage, int segv,
                                const void* d_desc, int n, long long items, int grid,
                                cudaStream_t st);
+// Scheduling state of the fused step kernel held by a handle.
+struct FusedRun {
+    unsigned* flags;             // fused_items(p) completion flags (device, zeroed once)
+    void* ctl;                   // fused_ctl_bytes() control block (device, zeroed once)
+    int* err_dev;                // device address of 3 host-mapped error words
+    unsigned long long wait_ns;  // bound of one device-side wait
+    int withhold;                // test hook: the first item withholds its first flag
+    int blocks_per_sm;           // 0: as many as fit
+};
+cudaError_t launch_fused_step(const teuk_params& p, const double* coef, double dt, double* u,
+                              double* w, int steps, const FusedRun& run, cudaStream_t st);
+size_t fused_items(const teuk_params& p);
+size_t fused_ctl_bytes();
+// Blocks of the fused kernel of p that fit on the device at once.
+cudaError_t fused_resident_blocks(const teuk_params& p, long long* blocks);
 }  // namespace teuk
 #endif

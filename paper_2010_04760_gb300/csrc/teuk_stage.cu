@@ -33,6 +33,24 @@ static unsigned pole_flip_of(const teuk_params& p) {
     return ((p.m + p.s) % 2 == 0) ? 0u : 0x80000000u;
 }
 
+// The fields of StageArgs that come from p alone (grid, epsilon, pole parity);
+// the pointers, step and stage weights are the caller's.
+void stage_args_common(StageArgs& A, const teuk_params& p) {
+    A.nr = p.nr;
+    A.nth = p.ntheta;
+    A.plane = (long long)p.nr * p.ntheta;
+    A.eps4 = 4.0 * p.eps;
+    eps_parts(p.eps, p.wprec, &A.eps_exp, &A.eps_pow2, &A.eps_mant);
+    A.pole_flip = pole_flip_of(p);
+    A.ko = 0.0;
+}
+
+void fused_layout(const teuk_params& p, int* nseg, int* nrb) {
+    const int seg = p.wprec == TEUK_W_FP64 ? Seg<TEUK_W_FP64>::value : Seg<TEUK_W_FP32>::value;
+    *nseg = (p.nr + seg - 1) / seg;
+    *nrb = (p.ntheta + WARPS - 1) / WARPS;
+}
+
 cudaError_t launch_stage(const teuk_params& p, const double* coef, const double* un,
                          const double* up, double* out, int stage, double dt,
                          cudaStream_t st) {
@@ -48,33 +66,26 @@ cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const doub
                             double beta, cudaStream_t st) {
     const int stage = kind > 2 ? 2 : kind;
     StageArgs A;
+    stage_args_common(A, p);
     A.coef = coef; A.un = un; A.up = up; A.out = out;
-    A.nr = p.nr; A.nth = p.ntheta;
-    A.plane = (long long)p.nr * p.ntheta;
     A.dt = h;
     A.alpha = alpha;
     A.beta = beta;
-    A.eps4 = 4.0 * p.eps;
-    eps_parts(p.eps, p.wprec, &A.eps_exp, &A.eps_pow2, &A.eps_mant);
-    A.pole_flip = pole_flip_of(p);
-    A.ko = 0.0;
     if (p.scheme == TEUK_SCHEME_FD6_KO8) {
         A.ko = h * p.ko_sigma / (256.0 * ((p.rstar_max - p.rstar_min) / (p.nr - 1)));
         dim3 grid((A.nr + 31) / 32, (A.nth + WARPS - 1) / WARPS), block(WARPS * 32);
         if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) {
             switch (stage) {
-            case 0: fd6_stage_kernel<0, true><<<grid, block, 0, st>>>(A); break;
-            case 1: fd6_stage_kernel<1, true><<<grid, block, 0, st>>>(A); break;
-            default: fd6_stage_kernel<2, true><<<grid, block, 0, st>>>(A); break;
-            }
-        } else {
-            switch (stage) {
-            case 0: fd6_stage_kernel<0><<<grid, block, 0, st>>>(A); break;
-            case 1: fd6_stage_kernel<1><<<grid, block, 0, st>>>(A); break;
-            default: fd6_stage_kernel<2><<<grid, block, 0, st>>>(A); break;
+            case 0: return launch_early(fd6_stage_kernel<0, true>, grid, block, A, st);
+            case 1: return launch_early(fd6_stage_kernel<1, true>, grid, block, A, st);
+            default: return launch_early(fd6_stage_kernel<2, true>, grid, block, A, st);
             }
         }
-        return cudaGetLastError();
+        switch (stage) {
+        case 0: return launch_early(fd6_stage_kernel<0>, grid, block, A, st);
+        case 1: return launch_early(fd6_stage_kernel<1>, grid, block, A, st);
+        default: return launch_early(fd6_stage_kernel<2>, grid, block, A, st);
+        }
     }
     const int th = p.theta_mode;
     if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) return launch_stage_hyp(A, p.wprec, th, stage, st);
@@ -84,6 +95,53 @@ cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const doub
     case TEUK_W_FP16: return launch_stage_w<TEUK_W_FP16>(A, stage, th, st);
     default: return launch_stage_w<TEUK_W_BF16>(A, stage, th, st);
     }
+}
+
+// `steps` SSP-RK(3,3) steps of p in one launch of the fused step kernel
+// (WENO5 radial scheme). w holds the two stage buffers (8 planes); flags,
+// ctl and err_dev are the handle's scheduling state (fused_items(p) flags, a
+// zeroed FusedCtl, host-mapped error words).
+cudaError_t launch_fused_step(const teuk_params& p, const double* coef, double dt, double* u,
+                              double* w, int steps, const FusedRun& run, cudaStream_t st) {
+    FusedArgs F;
+    stage_args_common(F.A, p);
+    F.A.coef = coef;
+    F.A.un = nullptr; F.A.up = nullptr; F.A.out = nullptr;
+    F.A.dt = stage_step(p, dt);
+    F.A.alpha = 0.0; F.A.beta = 1.0;
+    const size_t n = 4 * (size_t)p.nr * p.ntheta;
+    F.u = u; F.w1 = w; F.w2 = w + n;
+    fused_layout(p, &F.nseg, &F.nrb);
+    F.items = F.nseg * F.nrb;
+    F.epochs = 3 * steps;
+    F.flags = run.flags;
+    F.ctl = static_cast<FusedCtl*>(run.ctl);
+    F.err_host = run.err_dev;
+    F.wait_ns = run.wait_ns;
+    F.withhold = run.withhold;
+    if (p.coords == TEUK_COORDS_HYPERBOLOIDAL)
+        return launch_fused_hyp(F, p.wprec, p.theta_mode, run.blocks_per_sm, st);
+    return launch_fused_rstar(F, p.wprec, p.theta_mode, run.blocks_per_sm, st);
+}
+
+size_t fused_items(const teuk_params& p) {
+    int nseg = 0, nrb = 0;
+    fused_layout(p, &nseg, &nrb);
+    return (size_t)nseg * nrb;
+}
+
+size_t fused_ctl_bytes() { return sizeof(FusedCtl); }
+
+cudaError_t fused_resident_blocks(const teuk_params& p, long long* blocks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = p.coords == TEUK_COORDS_HYPERBOLOIDAL
+                ? fused_occupancy_hyp(p.wprec, p.theta_mode, &per_sm)
+                : fused_occupancy_rstar(p.wprec, p.theta_mode, &per_sm);
+    *blocks = (long long)sms * per_sm;
+    return e;
 }
 
 // SSP-RK(10,4) after its fifth stage (v = u4 + dt/6 F(u4)), in the two-register

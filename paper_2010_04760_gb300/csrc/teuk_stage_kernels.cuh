@@ -366,29 +366,42 @@ __device__ __forceinline__ double theta_weno_6hd(const double v[6], const StageA
 // Right-hand side and Runge-Kutta combination at node i0 + p of row j
 // (Sec. 2.3, Sec. 3.2). sw holds the segment's first differences and flux
 // terms. Loads use a clamped node index; the caller stores only real nodes.
-// 6h times the sixth-order centred derivative and the eighth difference
+// 60h times the sixth-order centred derivative and the eighth difference
 // delta^8 u at a node, from the first differences d[-4..3] around it
 // (d[m] = u_{j+m+1} - u_{j+m}):
 //   60 h u' = (d-3 + d2) - 8 (d-2 + d1) + 37 (d-1 + d0)     (Sec. 3.1.1 stencil)
 //   delta^8 u = (d3 - d-4) + 7 (d-3 - d2) + 21 (d1 - d-2) + 35 (d-1 - d0).
-__device__ __forceinline__ void fd6_ko8(const double* d, double& D6h, double& e8) {
+// The radial coefficient planes of this scheme carry 1/(60h).
+__device__ __forceinline__ void fd6_ko8(const double* d, double& D60h, double& e8) {
     const double t = fma(-8.0, d[2] + d[5], d[1] + d[6]);
-    D6h = 0.1 * fma(37.0, d[3] + d[4], t);
+    D60h = fma(37.0, d[3] + d[4], t);
     const double u = fma(7.0, d[1] - d[6], d[7] - d[0]);
     e8 = fma(35.0, d[3] - d[4], fma(21.0, d[5] - d[2], u));
+}
+
+// Load of a state value. The stage kernels read states that no thread writes
+// during the launch (read-only data path); the fused step kernel reads states
+// that other blocks of the same launch wrote, so it loads them from L2 (after
+// the acquire that orders those writes before the load).
+template <bool FUSED>
+__device__ __forceinline__ double ld_state(const double* p) {
+    if constexpr (FUSED) return __ldcg(p);
+    else return __ldg(p);
 }
 
 // Node k of a radial line f[0..nr) extended past either end (k in
 // [-4, nr+3]) by the quartic through the five edge nodes: the fifth
 // difference of the extended line vanishes, so each ghost follows from the
 // five values before it, u = 5 v0 - 10 v1 + 10 v2 - 5 v3 + v4 (v0 nearest).
+template <bool FUSED = false>
 static __device__ __noinline__ double ghost_value(const double* f, int nr, int k) {
-    if (k >= 0 && k < nr) return __ldg(f + k);
+    if (k >= 0 && k < nr) return ld_state<FUSED>(f + k);
     const bool left = k < 0;
     const int step = left ? 1 : -1;
     const int e = left ? 0 : nr - 1;
-    double v0 = __ldg(f + e), v1 = __ldg(f + e + step), v2 = __ldg(f + e + 2 * step);
-    double v3 = __ldg(f + e + 3 * step), v4 = __ldg(f + e + 4 * step);
+    double v0 = ld_state<FUSED>(f + e), v1 = ld_state<FUSED>(f + e + step);
+    double v2 = ld_state<FUSED>(f + e + 2 * step);
+    double v3 = ld_state<FUSED>(f + e + 3 * step), v4 = ld_state<FUSED>(f + e + 4 * step);
     const int n = left ? -k : k - (nr - 1);
     for (int t = 0; t < n; ++t) {
         const double u = fma(5.0, v0 - v3, fma(10.0, v2 - v1, v4));
@@ -399,7 +412,8 @@ static __device__ __noinline__ double ghost_value(const double* f, int nr, int k
 
 // HYP: the hyperboloidal slices, whose pi rows have their own speed (plane
 // kCc); in r* they share the Psi rows' b.
-template <int W, int STAGE, int THETA, class G, int SCHEME = 0, bool HYP = false>
+template <int W, int STAGE, int THETA, class G, int SCHEME = 0, bool HYP = false,
+          bool FUSED = false>
 __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw, int j,
                                             int i0, int p, double out[4]) {
     constexpr int NW = G::NW, FO = G::ND + G::NS;   // flux terms start at FO
@@ -408,7 +422,8 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     const long long P = A.plane;
     const long long q = (long long)j * nr + i;
     const double* cf = A.coef + q;
-    // 6 h D for each component (and the eighth differences of the FD6+KO8 scheme)
+    // 6 h D for each component (60 h D and the eighth differences for the
+    // FD6+KO8 scheme)
     double D0, D1, D2, D3, E0 = 0.0, E1 = 0.0, E2 = 0.0, E3 = 0.0;
     if constexpr (SCHEME == 1) {
         fd6_ko8(sw + 0 * NW + p, D0, E0);
@@ -421,8 +436,8 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
         D2 = fma(6.0, sw[2 * NW + p + 3], sw[2 * NW + FO + p + 1]) - sw[2 * NW + FO + p];
         D3 = fma(6.0, sw[3 * NW + p + 3], sw[3 * NW + FO + p + 1]) - sw[3 * NW + FO + p];
     }
-    const double psr = __ldg(A.up + q), psi = __ldg(A.up + P + q);
-    const double pir = __ldg(A.up + 2 * P + q), pii = __ldg(A.up + 3 * P + q);
+    const double psr = ld_state<FUSED>(A.up + q), psi = ld_state<FUSED>(A.up + P + q);
+    const double pir = ld_state<FUSED>(A.up + 2 * P + q), pii = ld_state<FUSED>(A.up + 3 * P + q);
     const double cb = __ldg(cf + kCb * P);
     const double cc = HYP ? __ldg(cf + kCc * P) : cb;
     const double cKr = __ldg(cf + kCKr * P);
@@ -455,8 +470,8 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
         const int jj = min(max(j + k, 0), A.nth - 1);   // weight is 0 off-grid
         const double w = __ldg(cf + (kW0 + k) * P);
         const long long qq = (long long)jj * nr + i;
-        acc2 = fma(w, __ldg(A.up + qq), acc2);
-        acc3 = fma(w, __ldg(A.up + P + qq), acc3);
+        acc2 = fma(w, ld_state<FUSED>(A.up + qq), acc2);
+        acc3 = fma(w, ld_state<FUSED>(A.up + P + qq), acc3);
     }
     if constexpr (THETA == TEUK_THETA_WENO5) {
         // Bth dPsi/dtheta with the WENO5 theta derivative, upwinded by the
@@ -472,8 +487,8 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
             if (jj < 0) { jj = -1 - jj; flip = A.pole_flip; }
             if (jj >= A.nth) { jj = 2 * A.nth - 1 - jj; flip = A.pole_flip; }
             const long long qq = (long long)jj * nr + i;
-            v0[k] = flip_sign(__ldg(A.up + qq), flip);
-            v1[k] = flip_sign(__ldg(A.up + P + qq), flip);
+            v0[k] = flip_sign(ld_state<FUSED>(A.up + qq), flip);
+            v1[k] = flip_sign(ld_state<FUSED>(A.up + P + qq), flip);
         }
         const double c = flip_sign(cBt, pos ? 0u : 0x80000000u);
         acc2 = fma(c, theta_weno_6hd<W>(v0, A), acc2);
@@ -486,17 +501,22 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
         acc3 = fma(-A.ko, E3, acc3);
     }
     if (STAGE >= 2) {
-        acc0 = fma(A.beta, acc0, A.alpha * A.un[q]);
-        acc1 = fma(A.beta, acc1, A.alpha * A.un[P + q]);
-        acc2 = fma(A.beta, acc2, A.alpha * A.un[2 * P + q]);
-        acc3 = fma(A.beta, acc3, A.alpha * A.un[3 * P + q]);
+        const double* un = A.un + q;
+        const double n0 = FUSED ? __ldcg(un) : un[0], n1 = FUSED ? __ldcg(un + P) : un[P];
+        const double n2 = FUSED ? __ldcg(un + 2 * P) : un[2 * P];
+        const double n3 = FUSED ? __ldcg(un + 3 * P) : un[3 * P];
+        acc0 = fma(A.beta, acc0, A.alpha * n0);
+        acc1 = fma(A.beta, acc1, A.alpha * n1);
+        acc2 = fma(A.beta, acc2, A.alpha * n2);
+        acc3 = fma(A.beta, acc3, A.alpha * n3);
     }
     out[0] = acc0; out[1] = acc1; out[2] = acc2; out[3] = acc3;
 }
 
 // One warp's work: segment seg_blk (nodes seg_blk*SEG ..) of theta row j of
 // the evolution described by A. sw is the warp's shared-memory block.
-template <int W, int STAGE, int THETA, int SEGV, int SCHEME = 0, bool HYP = false>
+template <int W, int STAGE, int THETA, int SEGV, int SCHEME = 0, bool HYP = false,
+          bool FUSED = false>
 __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, int lane, int j,
                                                 int seg_blk) {
     using G = std::conditional_t<SCHEME == 1, GeoFD<SEGV>, Geo<SEGV>>;
@@ -517,11 +537,12 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
         const double* f = A.up + c * A.plane + row;
         if (HYP && (g < 0 || g >= nr - 1)) {
             // nodes beyond nr-1+HALO feed no stored node
-            DL(c, k) = g + 1 <= nr - 1 + HALO ? ghost_value(f, nr, g + 1) - ghost_value(f, nr, g)
-                                              : 0.0;
+            DL(c, k) = g + 1 <= nr - 1 + HALO
+                           ? ghost_value<FUSED>(f, nr, g + 1) - ghost_value<FUSED>(f, nr, g)
+                           : 0.0;
         } else {
             const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
-            DL(c, k) = __ldg(f + ib) - __ldg(f + ia);
+            DL(c, k) = ld_state<FUSED>(f + ib) - ld_state<FUSED>(f + ia);
         }
     }
     __syncwarp();
@@ -544,9 +565,9 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
     //    predicated)
     for (int p = lane; p < SEG; p += 64) {
         double ua[4], ub[4];
-        node_update<W, STAGE, THETA, G, SCHEME, HYP>(A, sw, j, i0, p, ua);
+        node_update<W, STAGE, THETA, G, SCHEME, HYP, FUSED>(A, sw, j, i0, p, ua);
         const bool has_b = p + 32 < SEG;
-        if (has_b) node_update<W, STAGE, THETA, G, SCHEME, HYP>(A, sw, j, i0, p + 32, ub);
+        if (has_b) node_update<W, STAGE, THETA, G, SCHEME, HYP, FUSED>(A, sw, j, i0, p + 32, ub);
         const long long P = A.plane;
         if (i0 + p < nr) {
             const long long q = row + i0 + p;
@@ -590,6 +611,7 @@ template <int STAGE, bool HYP = false>
 __global__ void TEUK_BOUNDS fd6_stage_kernel(const StageArgs A) {
     constexpr int SEGV = 32;
     __shared__ double sm[WARPS][4 * GeoFD<SEGV>::NW];
+    dependent_launch_gate();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
@@ -719,6 +741,240 @@ cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, i
                ? launch_batch_wts<W, TEUK_THETA_CENTERED4, 64, HYP>(stage, d, n, items, grid, st)
                : launch_batch_wts<W, TEUK_THETA_CENTERED4, 32, HYP>(stage, d, n, items, grid, st);
 }
+
+// ---------------------------------------------------------------------------
+// Fused persistent step kernel: all SSP-RK(3,3) stages of `steps` steps of one
+// evolution in a single launch.
+//
+// A work item is a block of WARPS theta rows x one radial segment (the tile of
+// one stage_kernel block); epoch e = 3 (step) + (stage - 1). Tickets
+// t = e * items + item are handed out in increasing order by an atomic
+// counter. An item of epoch e reads, through its radial (+-3 nodes) and theta
+// (+-2 rows, +-3 with theta-WENO, reflected at the poles) stencils, only
+// nodes of its own and the eight neighbouring items, so it may start as soon
+// as those nine have completed epoch e - 1. That also orders every overwrite
+// after the reads of the old value: the stage buffer w1 (written in stage 1)
+// was last read by stage 2 of the previous step at the neighbours, w2 by
+// stage 3 at the neighbours, and u (written in stage 3) by stage 1 at the
+// neighbours and stage 2 at the item itself, all of which precede epoch e - 1
+// of the neighbours in the dependency chain. No block waits for a ticket above
+// its own, and every ticket below it is held by a running block, so the
+// smallest unfinished ticket can always proceed: the launch needs no
+// co-residency guarantee.
+//
+// Completion of epoch e at an item is published as flags[item] = base + e + 1
+// (a release store after a device-scope fence); a block waits for
+// flags[neighbour] >= base + e with acquire loads. `base` grows by the number
+// of epochs after every launch, so flags left by earlier launches never
+// satisfy a wait. Each wait is bounded by wait_ns of %globaltimer; when it
+// runs out the block records the item and epoch in host-mapped memory, raises
+// `abort`, and every block stops at its next check, so the launch ends and the
+// host reports TEUK_ERR_TIMEOUT. The last block to finish resets the ticket
+// counter and advances `base` for the next launch.
+// ---------------------------------------------------------------------------
+struct FusedCtl {
+    unsigned long long ticket;   // next ticket of the running launch
+    unsigned done;               // blocks that have left the running launch
+    unsigned base;               // epoch base of the running launch
+    int abort;                   // a wait ran out: every block stops
+    int pad;
+};
+
+struct FusedArgs {
+    StageArgs A;                 // grid, coefficients, weights' epsilon, pole parity, dt
+    double* u;                   // state u^n (updated in place by stage 3)
+    double* w1;                  // stage buffers
+    double* w2;
+    int nseg, nrb;               // radial segments, theta-row blocks
+    int items;                   // nseg * nrb
+    int epochs;                  // 3 x steps
+    unsigned* flags;             // [items]
+    FusedCtl* ctl;
+    int* err_host;               // host-mapped {code, epoch, item}; code 1 = timeout
+    unsigned long long wait_ns;  // bound of one dependency wait
+    int withhold;                // test hook: item 0 does not publish epoch 0
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Lanes 0..8 of warp 0: wait until neighbour (rb + lane/3 - 1, sg + lane%3 - 1)
+// has completed epoch e - 1. Returns false (warp-uniform) if a wait ran out or
+// another block raised abort.
+__device__ __forceinline__ bool wait_neighbours(const FusedArgs& F, unsigned base, int e, int rb,
+                                                int sg, int item, int lane) {
+    int ok = *(volatile int*)&F.ctl->abort ? 0 : 1;
+    if (ok && e > 0 && lane < 9) {
+        const int r = rb + lane / 3 - 1, g = sg + lane % 3 - 1;
+        if (r >= 0 && r < F.nrb && g >= 0 && g < F.nseg) {
+            const unsigned* f = F.flags + (long long)r * F.nseg + g;
+            const unsigned need = base + (unsigned)e;
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                if ((int)(ld_acquire_u32(f) - need) >= 0) break;
+                if (*(volatile int*)&F.ctl->abort) { ok = 0; break; }
+                if (global_ns() - t0 > F.wait_ns) {
+                    ok = 0;
+                    if (atomicCAS(&F.ctl->abort, 0, 1) == 0) {
+                        volatile int* eh = F.err_host;
+                        eh[1] = e;
+                        eh[2] = item;
+                        __threadfence_system();
+                        eh[0] = 1;
+                    }
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
+template <int W, int THETA, bool HYP>
+__global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
+    constexpr int SEGV = Seg<W>::value;
+    __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
+    __shared__ long long s_ticket;
+    __shared__ int s_go;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned base = *(volatile unsigned*)&F.ctl->base;
+    const long long total = (long long)F.items * F.epochs;
+    unsigned long long next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(&F.ctl->ticket, 1ULL);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long t = next;
+            if ((long long)t < total) next = atomicAdd(&F.ctl->ticket, 1ULL);   // next one early
+            s_ticket = (long long)t;
+        }
+        __syncthreads();
+        const long long t = s_ticket;
+        if (t >= total) break;
+        const int e = (int)(t / F.items);
+        const int item = (int)(t - (long long)e * F.items);
+        const int rb = item / F.nseg, sg = item - rb * F.nseg;
+        if (warp == 0) {
+            const bool go = wait_neighbours(F, base, e, rb, sg, item, lane);
+            if (lane == 0) s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int stage = e % 3 + 1;
+        StageArgs A = F.A;
+        if (stage == 1) { A.un = nullptr; A.up = F.u; A.out = F.w1; A.alpha = 0.0; A.beta = 1.0; }
+        if (stage == 2) { A.un = F.u; A.up = F.w1; A.out = F.w2; A.alpha = 0.75; A.beta = 0.25; }
+        if (stage == 3) {
+            A.un = F.u; A.up = F.w2; A.out = F.u; A.alpha = 1.0 / 3.0; A.beta = 2.0 / 3.0;
+        }
+        const int j = rb * WARPS + warp;
+        if (j < A.nth) {
+            if (stage == 1) process_segment<W, 1, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
+            else process_segment<W, 2, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
+        }
+        __syncthreads();            // every row's stores of this item are issued
+        if (threadIdx.x == 0 && !(F.withhold && e == 0 && item == 0)) {
+            __threadfence();
+            st_release_u32(F.flags + item, base + (unsigned)e + 1u);
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&F.ctl->done, 1u) == gridDim.x - 1) {    // last block of the launch
+            F.ctl->ticket = 0ULL;
+            F.ctl->done = 0u;
+            F.ctl->base = base + (unsigned)F.epochs;
+            F.ctl->abort = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int W, int THETA, bool HYP>
+cudaError_t launch_fused_wt(const FusedArgs& F, int blocks_per_sm_cap, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_kernel<W, THETA, HYP>,
+                                                          WARPS * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm_cap > 0) per_sm = std::min(per_sm, blocks_per_sm_cap);
+    const int grid = (int)std::max(1LL, std::min<long long>((long long)sms * per_sm, F.items));
+    fused_step_kernel<W, THETA, HYP><<<grid, WARPS * 32, 0, st>>>(F);
+    return cudaGetLastError();
+}
+
+// Resident blocks per SM of the fused kernel for (wprec, theta).
+template <bool HYP>
+cudaError_t fused_occupancy_h(int wprec, int theta, int* per_sm) {
+    const bool tw = theta == TEUK_THETA_WENO5;
+    const int nt = WARPS * 32;
+    switch (wprec) {
+    case TEUK_W_FP64:
+        return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_FP64, TEUK_THETA_WENO5, HYP>, nt, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_FP64, TEUK_THETA_CENTERED4, HYP>, nt, 0);
+    case TEUK_W_FP32:
+        return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_FP32, TEUK_THETA_WENO5, HYP>, nt, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_FP32, TEUK_THETA_CENTERED4, HYP>, nt, 0);
+    case TEUK_W_FP16:
+        return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_FP16, TEUK_THETA_WENO5, HYP>, nt, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_FP16, TEUK_THETA_CENTERED4, HYP>, nt, 0);
+    default:
+        return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_BF16, TEUK_THETA_WENO5, HYP>, nt, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        per_sm, fused_step_kernel<TEUK_W_BF16, TEUK_THETA_CENTERED4, HYP>, nt, 0);
+    }
+}
+
+template <bool HYP>
+cudaError_t launch_fused_h(const FusedArgs& F, int wprec, int theta, int cap, cudaStream_t st) {
+    const bool tw = theta == TEUK_THETA_WENO5;
+    switch (wprec) {
+    case TEUK_W_FP64:
+        return tw ? launch_fused_wt<TEUK_W_FP64, TEUK_THETA_WENO5, HYP>(F, cap, st)
+                  : launch_fused_wt<TEUK_W_FP64, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+    case TEUK_W_FP32:
+        return tw ? launch_fused_wt<TEUK_W_FP32, TEUK_THETA_WENO5, HYP>(F, cap, st)
+                  : launch_fused_wt<TEUK_W_FP32, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+    case TEUK_W_FP16:
+        return tw ? launch_fused_wt<TEUK_W_FP16, TEUK_THETA_WENO5, HYP>(F, cap, st)
+                  : launch_fused_wt<TEUK_W_FP16, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+    default:
+        return tw ? launch_fused_wt<TEUK_W_BF16, TEUK_THETA_WENO5, HYP>(F, cap, st)
+                  : launch_fused_wt<TEUK_W_BF16, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+    }
+}
+
+// teuk_stage.cu: the StageArgs fields that depend on p alone, and the work
+// items of the fused step kernel (radial segments x theta-row blocks).
+void stage_args_common(StageArgs& A, const teuk_params& p);
+void fused_layout(const teuk_params& p, int* nseg, int* nrb);
+// teuk_fused.cu / teuk_fused_hyp.cu: fused step launches per coordinate system.
+cudaError_t launch_fused_rstar(const FusedArgs& F, int wprec, int theta, int cap,
+                               cudaStream_t st);
+cudaError_t launch_fused_hyp(const FusedArgs& F, int wprec, int theta, int cap,
+                             cudaStream_t st);
+cudaError_t fused_occupancy_rstar(int wprec, int theta, int* per_sm);
+cudaError_t fused_occupancy_hyp(int wprec, int theta, int* per_sm);
 
 // Hyperboloidal-slice kernels, single evolution and batches (teuk_stage_hyp.cu).
 cudaError_t launch_stage_hyp(const StageArgs& A, int wprec, int theta, int stage,

@@ -432,3 +432,19 @@ def test_product_code_never_touches_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(text), os.path.join(dirpath, f)
+
+
+def test_fd6_radial_planes_carry_sixty_h():
+    """The FD6 + KO8 kernel forms 60 h D (the sixth-order stencil's own
+    normalisation, Sec. 3.1.1), so its radial planes (b, Re K, Im K) carry
+    dt/(60h) where the WENO5 planes carry dt/(6h); the others are the same."""
+    for coords in (T.TEUK_COORDS_RSTAR, T.TEUK_COORDS_HYPERBOLOIDAL):
+        kw = dict(a=0.7, s=-2, m=1, coords=coords)
+        weno = T.teuk_build_coefficients(T.make_params(64, 8, **kw), 0.01)
+        fd6 = T.teuk_build_coefficients(T.make_params(64, 8, scheme=1, **kw), 0.01)
+        radial = [0, 1, 2] + ([12] if coords == T.TEUK_COORDS_HYPERBOLOIDAL else [])
+        for k in range(weno.shape[0]):
+            if k in radial:
+                np.testing.assert_allclose(fd6[k], weno[k] / 10.0, rtol=1e-15, atol=0)
+            else:
+                np.testing.assert_array_equal(fd6[k], weno[k])

@@ -70,8 +70,9 @@ MUTANTS = [
      "const double sigma = ((p->m + p->s) % 2 == 0) ? -1.0 : 1.0;"),
     ("theta planes: pole mirror on the node", "if (jj < 0) tgt = -1 - jj;",
      "if (jj < 0) tgt = -jj;"),
-    ("radial planes: dt/(3h) for dt/(6h)", "const double c6h = dt / (6.0 * h);",
-     "const double c6h = dt / (3.0 * h);"),
+    ("radial planes: dt/(3h) for dt/(6h)",
+     "const double c6h = dt / ((p->scheme == TEUK_SCHEME_FD6_KO8 ? 60.0 : 6.0) * h);",
+     "const double c6h = dt / ((p->scheme == TEUK_SCHEME_FD6_KO8 ? 60.0 : 3.0) * h);"),
     ("radial spacing over nr", "const double h = (p->rstar_max - p->rstar_min) / (nr - 1);",
      "const double h = (p->rstar_max - p->rstar_min) / nr;"),
 ]
