@@ -42,15 +42,16 @@ FP64_FLOPS_PER_PT_STAGE = 112.0
 # algorithmic HBM bytes per point-stage: 11 coefficient planes (88 B), u_prev
 # (32 B), u_out (32 B), u^n in stages 2 and 3 (2/3 x 32 B).
 BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
-# DRAM bytes (read + write) per launch of the binary32-weight stage kernel,
-# averaged over the three stages, from one ncu capture of this workload on
-# these kernel sources; valid only for the sources it was taken on, identified
-# by the sha256 of their concatenation.
+# DRAM bytes (read + write) per launch of the binary32-weight kernel on this
+# workload, from one ncu capture on these kernel sources: the fused step kernel
+# (one launch = one step), averaged over three launches; valid only for the
+# sources it was taken on, identified by the sha256 of their concatenation.
 NCU_TRAFFIC = {"sources": ["paper_2010_04760_gb300/csrc/teuk_stage_kernels.cuh",
                            "paper_2010_04760_gb300/csrc/teuk_stage.cu"],
-               "sha256": "c32d877859ddf5d6692fcc9053d184f524b8287fad2f7fa28bf4d6d877cde37c",
-               "bytes_per_launch": (31478272 + 39867392 + 39868416) / 3.0,
-               "fused_bytes_per_launch": None}
+               "sha256": "32c562019b890f5a21088ce0b904aa782d8bce903066fbb6730fbcce68ab8e18",
+               "bytes_per_launch": None,
+               "fused_bytes_per_launch": (31502592 + 11776 + 31503104 + 26112 + 31503872
+                                          + 5888) / 3.0}
 
 
 def workload_config(wl, wprec):
@@ -108,7 +109,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -189,7 +190,7 @@ def time_gpu_steps(T, torch, wprec, steps, warmup, stream, flush, launch=None):
     stream.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
-    torch.cuda.nvtx.range_push(f"{wprec}_timed")
+    torch.cuda.nvtx.range_push(f"{wprec}_timed" + ("" if launch is None else f"_launch{launch}"))
     with torch.cuda.stream(stream):
         for k in range(steps):
             flush.fill_(float(k))                 # write > L2 between timed steps
@@ -234,12 +235,14 @@ def time_multi_step(T, torch, wprec, steps, warmup, stream, flush):
     T.teuk_step(h, max(warmup, 4))
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push(f"{wprec}_multi_timed")
     with torch.cuda.stream(stream):
         flush.fill_(1)
         e0.record(stream)
         T.teuk_step(h, steps)
         e1.record(stream)
     stream.synchronize()
+    torch.cuda.nvtx.range_pop()
     assert T.teuk_check_finite(h) == T.TEUK_OK
     h.close()
     return e0.elapsed_time(e1)

@@ -116,9 +116,9 @@ typedef enum {
 
 /* How teuk_step launches a step (see teuk_set_launch). */
 typedef enum {
-    TEUK_LAUNCH_AUTO = 0,     /* the fused step for calls of >= 4 steps on grids
-                                 with at least as many work items per stage as
-                                 the device holds blocks, else stages           */
+    TEUK_LAUNCH_AUTO = 0,     /* the fused step on grids with at least as many
+                                 work items per stage as the device holds
+                                 blocks (SSP-RK(3,3) with WENO5), else stages  */
     TEUK_LAUNCH_STAGES = 1,   /* one launch per Runge-Kutta stage (CUDA graph)  */
     TEUK_LAUNCH_FUSED = 2     /* one persistent launch for all stages of up to
                                  1024 steps (SSP-RK(3,3) with WENO5 only)       */
@@ -326,9 +326,9 @@ teuk_status teuk_get_state_async(teuk_handle* h, double* u_host);
 teuk_status teuk_synchronize(teuk_handle* h);
 
 /* Advance nsteps steps of p's integrator. With the fused step (by default
- * for SSP-RK(3,3) with WENO5 when nsteps >= 4 and the grid has at least as
- * many work items per stage as resident blocks; see teuk_set_launch) one
- * persistent launch runs
+ * for SSP-RK(3,3) with WENO5 when the grid has at least as many work items
+ * per stage as resident blocks; see teuk_set_launch) one persistent launch
+ * runs
  * every stage of up to 1024 steps: work items (4 theta rows x one radial
  * segment) are taken in stage order, and an item starts as soon as the eight
  * items around it have finished the previous stage, so stages overlap
@@ -352,10 +352,10 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps);
 teuk_status teuk_set_launch(teuk_handle* h, int mode, double wait_seconds);
 
 /* The launch mode set by teuk_set_launch (TEUK_LAUNCH_AUTO unless changed),
- * the wait bound, and the smallest nsteps for which teuk_step uses the fused
- * step (1, 4, or 0 for never). Any output may be NULL. */
+ * the wait bound, and whether teuk_step uses the fused step (1) or stage
+ * launches (0). Any output may be NULL. */
 teuk_status teuk_get_launch(const teuk_handle* h, int* mode_out, double* wait_seconds_out,
-                            int64_t* fused_from_steps_out);
+                            int* fused_out);
 
 /* Test hook for the timeout path (no counterpart in the paper): the next
  * fused launch of h does not publish the completion of its first work item's

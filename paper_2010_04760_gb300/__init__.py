@@ -390,8 +390,8 @@ def teuk_set_launch(h, mode, wait_seconds=2.0):
 
 
 def teuk_get_launch(h):
-    """(mode, wait_seconds, smallest nsteps run by the fused step or 0)."""
-    mode, wait, k = ctypes.c_int(), ctypes.c_double(), ctypes.c_int64()
+    """(mode, wait_seconds, 1 if teuk_step uses the fused step else 0)."""
+    mode, wait, k = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
     _check(lib().teuk_get_launch(h.ptr, ctypes.byref(mode), ctypes.byref(wait),
                                  ctypes.byref(k)))
     return mode.value, wait.value, k.value

@@ -173,17 +173,14 @@ struct teuk_handle {
     long long fused_items = 0, fused_blocks = 0;   // work items per stage, resident blocks
     size_t plane() const { return (size_t)p.nr * p.ntheta; }
     bool fused_ok() const { return p.rk == TEUK_RK_SSP33 && p.scheme == TEUK_SCHEME_WENO5; }
-    // The schedule of a teuk_step call of nsteps steps. AUTO: the fused step
-    // for calls of at least kFusedMinSteps steps on grids with at least as
-    // many work items per stage as resident blocks; otherwise stage launches
-    // (a single step has too few stages to amortise the persistent launch's
-    // ramp and tail, and a smaller grid leaves blocks waiting on each other).
-    static constexpr int64_t kFusedMinSteps = 4;
-    int launch_for(int64_t nsteps) const {
+    // The schedule of teuk_step. AUTO: the fused step on grids with at least
+    // as many work items per stage as resident blocks (measured faster than
+    // stage launches from one step per call up); otherwise stage launches
+    // (on a smaller grid the blocks of consecutive stages wait on each other).
+    int launch_used() const {
         if (launch == TEUK_LAUNCH_STAGES || !fused_ok()) return TEUK_LAUNCH_STAGES;
         if (launch == TEUK_LAUNCH_FUSED) return TEUK_LAUNCH_FUSED;
-        return (nsteps >= kFusedMinSteps && fused_items >= fused_blocks) ? TEUK_LAUNCH_FUSED
-                                                                        : TEUK_LAUNCH_STAGES;
+        return fused_items >= fused_blocks ? TEUK_LAUNCH_FUSED : TEUK_LAUNCH_STAGES;
     }
 };
 
@@ -752,7 +749,7 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
         if (nsteps < 0) return fail(TEUK_ERR_ARG, "nsteps < 0");
         teuk_status ws = wait_status(h);          // an earlier launch that already ran out
         if (ws != TEUK_OK) return ws;
-        if (h->launch_for(nsteps) == TEUK_LAUNCH_FUSED) {
+        if (h->launch_used() == TEUK_LAUNCH_FUSED) {
             // one launch per 1024 steps (bounds a launch's duration)
             FusedRun run{h->fflags, h->fctl, h->err_dev,
                          (unsigned long long)(h->wait_s * 1e9), h->withhold, 0};
@@ -861,18 +858,12 @@ teuk_status teuk_set_launch(teuk_handle* h, int mode, double wait_seconds) {
 }
 
 teuk_status teuk_get_launch(const teuk_handle* h, int* mode_out, double* wait_seconds_out,
-                            int64_t* fused_from_steps_out) {
+                            int* fused_out) {
     return guarded("teuk_get_launch", [&]() -> teuk_status {
         if (!h) return fail(TEUK_ERR_ARG, "handle is NULL");
         if (mode_out) *mode_out = h->launch;
         if (wait_seconds_out) *wait_seconds_out = h->wait_s;
-        if (fused_from_steps_out) {
-            int64_t k = 0;
-            if (h->launch_for(1) == TEUK_LAUNCH_FUSED) k = 1;
-            else if (h->launch_for(teuk_handle::kFusedMinSteps) == TEUK_LAUNCH_FUSED)
-                k = teuk_handle::kFusedMinSteps;
-            *fused_from_steps_out = k;
-        }
+        if (fused_out) *fused_out = h->launch_used() == TEUK_LAUNCH_FUSED;
         return TEUK_OK;
     });
 }

@@ -5,9 +5,9 @@
 
 namespace teuk {
 
-cudaError_t launch_fused_rstar(const FusedArgs& F, int wprec, int theta, int cap,
+cudaError_t launch_fused_rstar(const FusedArgs& F, int wprec, int theta, int seg, int cap,
                                cudaStream_t st) {
-    return launch_fused_h<false>(F, wprec, theta, cap, st);
+    return launch_fused_h<false>(F, wprec, theta, seg, cap, st);
 }
 
 cudaError_t fused_occupancy_rstar(int wprec, int theta, int* per_sm) {

@@ -4,9 +4,9 @@
 
 namespace teuk {
 
-cudaError_t launch_fused_hyp(const FusedArgs& F, int wprec, int theta, int cap,
+cudaError_t launch_fused_hyp(const FusedArgs& F, int wprec, int theta, int seg, int cap,
                              cudaStream_t st) {
-    return launch_fused_h<true>(F, wprec, theta, cap, st);
+    return launch_fused_h<true>(F, wprec, theta, seg, cap, st);
 }
 
 cudaError_t fused_occupancy_hyp(int wprec, int theta, int* per_sm) {

@@ -46,7 +46,7 @@ void stage_args_common(StageArgs& A, const teuk_params& p) {
 }
 
 void fused_layout(const teuk_params& p, int* nseg, int* nrb) {
-    const int seg = p.wprec == TEUK_W_FP64 ? Seg<TEUK_W_FP64>::value : Seg<TEUK_W_FP32>::value;
+    const int seg = fused_seg(p.wprec, p.nr, p.ntheta);
     *nseg = (p.nr + seg - 1) / seg;
     *nrb = (p.ntheta + WARPS - 1) / WARPS;
 }
@@ -119,9 +119,10 @@ cudaError_t launch_fused_step(const teuk_params& p, const double* coef, double d
     F.err_host = run.err_dev;
     F.wait_ns = run.wait_ns;
     F.withhold = run.withhold;
+    const int seg = fused_seg(p.wprec, p.nr, p.ntheta);
     if (p.coords == TEUK_COORDS_HYPERBOLOIDAL)
-        return launch_fused_hyp(F, p.wprec, p.theta_mode, run.blocks_per_sm, st);
-    return launch_fused_rstar(F, p.wprec, p.theta_mode, run.blocks_per_sm, st);
+        return launch_fused_hyp(F, p.wprec, p.theta_mode, seg, run.blocks_per_sm, st);
+    return launch_fused_rstar(F, p.wprec, p.theta_mode, seg, run.blocks_per_sm, st);
 }
 
 size_t fused_items(const teuk_params& p) {

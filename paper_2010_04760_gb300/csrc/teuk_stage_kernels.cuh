@@ -748,8 +748,9 @@ cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, i
 //
 // A work item is a block of WARPS theta rows x one radial segment (the tile of
 // one stage_kernel block); epoch e = 3 (step) + (stage - 1). Tickets
-// t = e * items + item are handed out in increasing order by an atomic
-// counter. An item of epoch e reads, through its radial (+-3 nodes) and theta
+// t = e * items + item are handed out in increasing order: block b starts with
+// ticket b and takes each later one from an atomic counter (plus the grid
+// size) as soon as it reads its current one. An item of epoch e reads, through its radial (+-3 nodes) and theta
 // (+-2 rows, +-3 with theta-WENO, reflected at the poles) stencils, only
 // nodes of its own and the eight neighbouring items, so it may start as soon
 // as those nine have completed epoch e - 1. That also orders every overwrite
@@ -842,21 +843,21 @@ __device__ __forceinline__ bool wait_neighbours(const FusedArgs& F, unsigned bas
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
-template <int W, int THETA, bool HYP>
+template <int W, int THETA, bool HYP, int SEGV>
 __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
-    constexpr int SEGV = Seg<W>::value;
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
     __shared__ long long s_ticket;
     __shared__ int s_go;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned base = *(volatile unsigned*)&F.ctl->base;
     const long long total = (long long)F.items * F.epochs;
-    unsigned long long next = 0;
-    if (threadIdx.x == 0) next = atomicAdd(&F.ctl->ticket, 1ULL);
+    // first ticket: the block's own index (no atomic traffic while the whole
+    // grid starts); later ones from the counter, offset by the grid size
+    unsigned long long next = blockIdx.x;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long t = next;
-            if ((long long)t < total) next = atomicAdd(&F.ctl->ticket, 1ULL);   // next one early
+            if ((long long)t < total) next = gridDim.x + atomicAdd(&F.ctl->ticket, 1ULL);
             s_ticket = (long long)t;
         }
         __syncthreads();
@@ -901,22 +902,46 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
     }
 }
 
-template <int W, int THETA, bool HYP>
-cudaError_t launch_fused_wt(const FusedArgs& F, int blocks_per_sm_cap, cudaStream_t st) {
+// Radial segment of the fused kernel: 64 nodes with binary64 weights; with
+// reduced-precision weights 32, or 64 on grids with at least kSeg64Items
+// 64-node work items per stage (three waves of resident blocks and more: the
+// halo phases idle fewer lanes per node, measured 6% faster on the
+// 8192 x 256 and 16384 x 64 grids, while the 2048 x 128 grid needs the 32-node
+// items to fill the device).
+constexpr long long kSeg64Items = 3 * 8 * 152;
+inline int fused_seg(int wprec, int nr, int ntheta) {
+    if (wprec == TEUK_W_FP64) return 64;
+    const long long items64 = (long long)((nr + 63) / 64) * ((ntheta + WARPS - 1) / WARPS);
+    return items64 >= kSeg64Items ? 64 : 32;
+}
+
+template <int W, int THETA, bool HYP, int SEGV>
+cudaError_t launch_fused_wts(const FusedArgs& F, int blocks_per_sm_cap, cudaStream_t st) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_kernel<W, THETA, HYP>,
-                                                          WARPS * 32, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, fused_step_kernel<W, THETA, HYP, SEGV>, WARPS * 32, 0);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm_cap > 0) per_sm = std::min(per_sm, blocks_per_sm_cap);
     const int grid = (int)std::max(1LL, std::min<long long>((long long)sms * per_sm, F.items));
-    fused_step_kernel<W, THETA, HYP><<<grid, WARPS * 32, 0, st>>>(F);
+    fused_step_kernel<W, THETA, HYP, SEGV><<<grid, WARPS * 32, 0, st>>>(F);
     return cudaGetLastError();
 }
 
-// Resident blocks per SM of the fused kernel for (wprec, theta).
+template <int W, int THETA, bool HYP>
+cudaError_t launch_fused_wt(const FusedArgs& F, int seg, int cap, cudaStream_t st) {
+    if constexpr (W == TEUK_W_FP64) {
+        return launch_fused_wts<W, THETA, HYP, 64>(F, cap, st);
+    } else {
+        return seg == 64 ? launch_fused_wts<W, THETA, HYP, 64>(F, cap, st)
+                         : launch_fused_wts<W, THETA, HYP, 32>(F, cap, st);
+    }
+}
+
+// Resident blocks per SM of the fused kernel (the same for both segment
+// lengths: 64 registers and at most 26 KB of shared memory per block).
 template <bool HYP>
 cudaError_t fused_occupancy_h(int wprec, int theta, int* per_sm) {
     const bool tw = theta == TEUK_THETA_WENO5;
@@ -924,43 +949,36 @@ cudaError_t fused_occupancy_h(int wprec, int theta, int* per_sm) {
     switch (wprec) {
     case TEUK_W_FP64:
         return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_FP64, TEUK_THETA_WENO5, HYP>, nt, 0)
+                        per_sm, fused_step_kernel<TEUK_W_FP64, TEUK_THETA_WENO5, HYP, 64>, nt, 0)
                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_FP64, TEUK_THETA_CENTERED4, HYP>, nt, 0);
-    case TEUK_W_FP32:
-        return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_FP32, TEUK_THETA_WENO5, HYP>, nt, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_FP32, TEUK_THETA_CENTERED4, HYP>, nt, 0);
-    case TEUK_W_FP16:
-        return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_FP16, TEUK_THETA_WENO5, HYP>, nt, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_FP16, TEUK_THETA_CENTERED4, HYP>, nt, 0);
+                        per_sm, fused_step_kernel<TEUK_W_FP64, TEUK_THETA_CENTERED4, HYP, 64>,
+                        nt, 0);
     default:
         return tw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_BF16, TEUK_THETA_WENO5, HYP>, nt, 0)
+                        per_sm, fused_step_kernel<TEUK_W_FP32, TEUK_THETA_WENO5, HYP, 64>, nt, 0)
                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        per_sm, fused_step_kernel<TEUK_W_BF16, TEUK_THETA_CENTERED4, HYP>, nt, 0);
+                        per_sm, fused_step_kernel<TEUK_W_FP32, TEUK_THETA_CENTERED4, HYP, 64>,
+                        nt, 0);
     }
 }
 
 template <bool HYP>
-cudaError_t launch_fused_h(const FusedArgs& F, int wprec, int theta, int cap, cudaStream_t st) {
+cudaError_t launch_fused_h(const FusedArgs& F, int wprec, int theta, int seg, int cap,
+                           cudaStream_t st) {
     const bool tw = theta == TEUK_THETA_WENO5;
     switch (wprec) {
     case TEUK_W_FP64:
-        return tw ? launch_fused_wt<TEUK_W_FP64, TEUK_THETA_WENO5, HYP>(F, cap, st)
-                  : launch_fused_wt<TEUK_W_FP64, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+        return tw ? launch_fused_wt<TEUK_W_FP64, TEUK_THETA_WENO5, HYP>(F, seg, cap, st)
+                  : launch_fused_wt<TEUK_W_FP64, TEUK_THETA_CENTERED4, HYP>(F, seg, cap, st);
     case TEUK_W_FP32:
-        return tw ? launch_fused_wt<TEUK_W_FP32, TEUK_THETA_WENO5, HYP>(F, cap, st)
-                  : launch_fused_wt<TEUK_W_FP32, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+        return tw ? launch_fused_wt<TEUK_W_FP32, TEUK_THETA_WENO5, HYP>(F, seg, cap, st)
+                  : launch_fused_wt<TEUK_W_FP32, TEUK_THETA_CENTERED4, HYP>(F, seg, cap, st);
     case TEUK_W_FP16:
-        return tw ? launch_fused_wt<TEUK_W_FP16, TEUK_THETA_WENO5, HYP>(F, cap, st)
-                  : launch_fused_wt<TEUK_W_FP16, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+        return tw ? launch_fused_wt<TEUK_W_FP16, TEUK_THETA_WENO5, HYP>(F, seg, cap, st)
+                  : launch_fused_wt<TEUK_W_FP16, TEUK_THETA_CENTERED4, HYP>(F, seg, cap, st);
     default:
-        return tw ? launch_fused_wt<TEUK_W_BF16, TEUK_THETA_WENO5, HYP>(F, cap, st)
-                  : launch_fused_wt<TEUK_W_BF16, TEUK_THETA_CENTERED4, HYP>(F, cap, st);
+        return tw ? launch_fused_wt<TEUK_W_BF16, TEUK_THETA_WENO5, HYP>(F, seg, cap, st)
+                  : launch_fused_wt<TEUK_W_BF16, TEUK_THETA_CENTERED4, HYP>(F, seg, cap, st);
     }
 }
 
@@ -969,9 +987,9 @@ cudaError_t launch_fused_h(const FusedArgs& F, int wprec, int theta, int cap, cu
 void stage_args_common(StageArgs& A, const teuk_params& p);
 void fused_layout(const teuk_params& p, int* nseg, int* nrb);
 // teuk_fused.cu / teuk_fused_hyp.cu: fused step launches per coordinate system.
-cudaError_t launch_fused_rstar(const FusedArgs& F, int wprec, int theta, int cap,
+cudaError_t launch_fused_rstar(const FusedArgs& F, int wprec, int theta, int seg, int cap,
                                cudaStream_t st);
-cudaError_t launch_fused_hyp(const FusedArgs& F, int wprec, int theta, int cap,
+cudaError_t launch_fused_hyp(const FusedArgs& F, int wprec, int theta, int seg, int cap,
                              cudaStream_t st);
 cudaError_t fused_occupancy_rstar(int wprec, int theta, int* per_sm);
 cudaError_t fused_occupancy_hyp(int wprec, int theta, int* per_sm);

@@ -47,6 +47,9 @@ CASES = [
     (I.EXTREMAL_GRAV_HYP.with_(nr=1500, nth=22), "fp32", 0, 8),    # horizon to scri
     (I.EXTREMAL_GRAV_HYP.with_(nr=700, nth=9), "bf16", 1, 5),
     (I.EXTREMAL_GRAV_HYP.with_(nr=300, nth=16), "fp64", 0, 4),
+    # grids with enough 64-node items that the fused kernel takes 64-node segments
+    (I.EXTREMAL_GRAV_HYP, "fp32", 0, 3),                           # the paper's 16384 x 64
+    (I.EXTREMAL_SCALAR, "bf16", 0, 2),                             # 8192 x 256
 ]
 
 
@@ -80,12 +83,12 @@ def test_fused_step_across_launches_and_calls():
 
 
 def test_auto_launch_choice():
-    """AUTO: the fused step for calls of at least 4 steps on grids with at
-    least as many work items per stage as resident blocks (the benchmark grid,
-    2048 work items), stage launches otherwise (the 256 x 32 grid, 64 items;
-    binary64 weights on the benchmark grid, 1024 items of 64-node segments)."""
+    """AUTO: the fused step on grids with at least as many work items per
+    stage as resident blocks (the benchmark grid, 2048 work items), stage
+    launches otherwise (the 256 x 32 grid, 64 items; binary64 weights on the
+    benchmark grid, 1024 items of 64-node segments)."""
     h = T.teuk_create(T.params_from_workload(I.KERR_GRAV, wprec="fp32"))
-    assert T.teuk_get_launch(h) == (T.TEUK_LAUNCH_AUTO, 2.0, 4)
+    assert T.teuk_get_launch(h) == (T.TEUK_LAUNCH_AUTO, 2.0, 1)
     h = T.teuk_create(T.params_from_workload(I.KERR_GRAV, wprec="fp64"))
     assert T.teuk_get_launch(h) == (T.TEUK_LAUNCH_AUTO, 2.0, 0)
     p = T.params_from_workload(I.SCHW_SCALAR)
