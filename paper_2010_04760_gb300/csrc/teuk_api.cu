@@ -171,6 +171,8 @@ struct teuk_handle {
     double wait_s = 2.0;
     int withhold = 0;
     long long fused_items = 0, fused_blocks = 0;   // work items per stage, resident blocks
+    unsigned fused_base = 0;                       // epochs of the fused launches so far
+    int fused_parity = 0;                          // fused launches so far, mod 2
     size_t plane() const { return (size_t)p.nr * p.ntheta; }
     bool fused_ok() const { return p.rk == TEUK_RK_SSP33 && p.scheme == TEUK_SCHEME_WENO5; }
     // The schedule of teuk_step. AUTO: the fused step on grids with at least
@@ -752,10 +754,14 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps) {
         if (h->launch_used() == TEUK_LAUNCH_FUSED) {
             // one launch per 1024 steps (bounds a launch's duration)
             FusedRun run{h->fflags, h->fctl, h->err_dev,
-                         (unsigned long long)(h->wait_s * 1e9), h->withhold, 0};
+                         (unsigned long long)(h->wait_s * 1e9), h->withhold, 0, 0u, 0};
             for (int64_t left = nsteps; left > 0;) {
                 const int k = (int)std::min<int64_t>(left, 1024);
+                run.base = h->fused_base;
+                run.parity = h->fused_parity;
                 TEUK_CUDA(launch_fused_step(h->p, h->coef, h->dt, h->u, h->w, k, run, h->stream));
+                h->fused_base += 3u * (unsigned)k;
+                h->fused_parity ^= 1;
                 run.withhold = 0;
                 h->withhold = 0;
                 left -= k;

@@ -107,6 +107,8 @@ struct FusedRun {
     unsigned long long wait_ns;  // bound of one device-side wait
     int withhold;                // test hook: the first item withholds its first flag
     int blocks_per_sm;           // 0: as many as fit
+    unsigned base;               // epochs completed by earlier launches (mod 2^32)
+    int parity;                  // launches so far, mod 2
 };
 cudaError_t launch_fused_step(const teuk_params& p, const double* coef, double dt, double* u,
                               double* w, int steps, const FusedRun& run, cudaStream_t st);

@@ -116,6 +116,8 @@ cudaError_t launch_fused_step(const teuk_params& p, const double* coef, double d
     F.epochs = 3 * steps;
     F.flags = run.flags;
     F.ctl = static_cast<FusedCtl*>(run.ctl);
+    F.base = run.base;
+    F.parity = run.parity;
     F.err_host = run.err_dev;
     F.wait_ns = run.wait_ns;
     F.withhold = run.withhold;

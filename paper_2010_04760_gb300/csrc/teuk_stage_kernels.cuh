@@ -765,20 +765,20 @@ cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, i
 //
 // Completion of epoch e at an item is published as flags[item] = base + e + 1
 // (a release store after a device-scope fence); a block waits for
-// flags[neighbour] >= base + e with acquire loads. `base` grows by the number
-// of epochs after every launch, so flags left by earlier launches never
-// satisfy a wait. Each wait is bounded by wait_ns of %globaltimer; when it
-// runs out the block records the item and epoch in host-mapped memory, raises
-// `abort`, and every block stops at its next check, so the launch ends and the
-// host reports TEUK_ERR_TIMEOUT. The last block to finish resets the ticket
-// counter and advances `base` for the next launch.
+// flags[neighbour] >= base + e with acquire loads. The host advances `base` by
+// the launch's epochs after every launch, so flags left by earlier launches
+// never satisfy a wait and nothing is cleared between launches. Each wait is
+// bounded by wait_ns of %globaltimer; when it runs out the block records the
+// item and epoch in host-mapped memory, raises `abort`, and every block stops
+// at its next check, so the launch ends and the host reports TEUK_ERR_TIMEOUT.
+// The ticket counter and the abort word come in two copies used by alternate
+// launches (`parity`, kept by the host): block 0 of a launch zeroes the other
+// copy, which the previous launch has finished with and the next one will
+// use, so no block has to meet the others at the end of a launch.
 // ---------------------------------------------------------------------------
 struct FusedCtl {
-    unsigned long long ticket;   // next ticket of the running launch
-    unsigned done;               // blocks that have left the running launch
-    unsigned base;               // epoch base of the running launch
-    int abort;                   // a wait ran out: every block stops
-    int pad;
+    unsigned long long ticket[2];   // next ticket, one per launch parity
+    int abort[2];                   // a wait ran out: every block stops
 };
 
 struct FusedArgs {
@@ -791,6 +791,8 @@ struct FusedArgs {
     int epochs;                  // 3 x steps
     unsigned* flags;             // [items]
     FusedCtl* ctl;
+    unsigned base;               // epoch base of this launch
+    int parity;                  // which ticket counter and abort word it uses
     int* err_host;               // host-mapped {code, epoch, item}; code 1 = timeout
     unsigned long long wait_ns;  // bound of one dependency wait
     int withhold;                // test hook: item 0 does not publish epoch 0
@@ -815,7 +817,8 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 // another block raised abort.
 __device__ __forceinline__ bool wait_neighbours(const FusedArgs& F, unsigned base, int e, int rb,
                                                 int sg, int item, int lane) {
-    int ok = *(volatile int*)&F.ctl->abort ? 0 : 1;
+    int* abort = &F.ctl->abort[F.parity];
+    int ok = *(volatile int*)abort ? 0 : 1;
     if (ok && e > 0 && lane < 9) {
         const int r = rb + lane / 3 - 1, g = sg + lane % 3 - 1;
         if (r >= 0 && r < F.nrb && g >= 0 && g < F.nseg) {
@@ -824,10 +827,10 @@ __device__ __forceinline__ bool wait_neighbours(const FusedArgs& F, unsigned bas
             const unsigned long long t0 = global_ns();
             for (;;) {
                 if ((int)(ld_acquire_u32(f) - need) >= 0) break;
-                if (*(volatile int*)&F.ctl->abort) { ok = 0; break; }
+                if (*(volatile int*)abort) { ok = 0; break; }
                 if (global_ns() - t0 > F.wait_ns) {
                     ok = 0;
-                    if (atomicCAS(&F.ctl->abort, 0, 1) == 0) {
+                    if (atomicCAS(abort, 0, 1) == 0) {
                         volatile int* eh = F.err_host;
                         eh[1] = e;
                         eh[2] = item;
@@ -849,15 +852,20 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
     __shared__ long long s_ticket;
     __shared__ int s_go;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned base = *(volatile unsigned*)&F.ctl->base;
+    const unsigned base = F.base;
     const long long total = (long long)F.items * F.epochs;
+    unsigned long long* counter = &F.ctl->ticket[F.parity];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {     // ready the other copy for the next launch
+        F.ctl->ticket[1 - F.parity] = 0ULL;
+        F.ctl->abort[1 - F.parity] = 0;
+    }
     // first ticket: the block's own index (no atomic traffic while the whole
     // grid starts); later ones from the counter, offset by the grid size
     unsigned long long next = blockIdx.x;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long t = next;
-            if ((long long)t < total) next = gridDim.x + atomicAdd(&F.ctl->ticket, 1ULL);
+            if ((long long)t < total) next = gridDim.x + atomicAdd(counter, 1ULL);
             s_ticket = (long long)t;
         }
         __syncthreads();
@@ -888,16 +896,6 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
         if (threadIdx.x == 0 && !(F.withhold && e == 0 && item == 0)) {
             __threadfence();
             st_release_u32(F.flags + item, base + (unsigned)e + 1u);
-        }
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&F.ctl->done, 1u) == gridDim.x - 1) {    // last block of the launch
-            F.ctl->ticket = 0ULL;
-            F.ctl->done = 0u;
-            F.ctl->base = base + (unsigned)F.epochs;
-            F.ctl->abort = 0;
-            __threadfence();
         }
     }
 }
