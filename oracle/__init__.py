@@ -239,3 +239,83 @@ def observe(g, u, rs_ext):
     hor = np.zeros((g.nth, 6))
     _load().orc_observe(ctypes.byref(g), _ptr(u), rs_ext, _ptr(wave), _ptr(hor))
     return wave, hor
+
+
+# ---------------------------------------------------------------------------
+# Extended-precision state (teuk_oracle_ld.c): the same right-hand side and
+# SSP-RK(3,3) step with the state, weights and fluxes in C long double
+# (binary128 on aarch64, the x87 64-bit-significand format on x86-64), for
+# measuring the binary64 state's own round-off. Arrays are numpy longdouble,
+# which is C long double on both.
+# ---------------------------------------------------------------------------
+_SRC_LD = os.path.join(_HERE, "teuk_oracle_ld.c")
+_LIB_LD = os.path.join(_HERE, "libteuk_oracle_ld.so")
+_lib_ld = None
+
+
+def build_ld(force=False, src=_SRC_LD, out=_LIB_LD):
+    """Compile the extended-precision oracle (same flags as the binary64 one;
+    ``src``/``out`` as for ``build``)."""
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                           "-I", _HERE, "-o", out, src, "-lm"])
+    return out
+
+
+def _load_ld():
+    global _lib_ld
+    if _lib_ld is None:
+        # TEUK_ORACLE_LD_LIB: a prebuilt copy to load instead (mutation tests)
+        lib = ctypes.CDLL(os.environ.get("TEUK_ORACLE_LD_LIB") or build_ld())
+        I, D, L, P = ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_void_p
+        sig = {"orc_ld_mant_dig": (I, []),
+               "orc_ld_weno5_flux": (None, [I, P, P, P]),
+               "orc_ld_rhs": (I, [P, P, P, P]),
+               "orc_ld_rk3_step": (I, [P, P, D, P, L])}
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib_ld = lib
+    return _lib_ld
+
+
+def _ld(a):
+    return np.ascontiguousarray(a, dtype=np.longdouble)
+
+
+def ld_mant_dig():
+    """Significand bits of the extended state (113 binary128, 64 x87)."""
+    return _load_ld().orc_ld_mant_dig()
+
+
+def ld_weno5_flux(f5, dir, eps=1e-6):
+    """WENO5 flux of five long double values (dir +1: f_{j-2..j+2}, dir -1:
+    f_{j-1..j+3}; the interface j+1/2 either way)."""
+    f5 = _ld(f5)
+    e = np.array([eps], dtype=np.longdouble)
+    out = np.zeros(1, dtype=np.longdouble)
+    _load_ld().orc_ld_weno5_flux(int(dir), _ptr(f5), _ptr(e), _ptr(out))
+    return out[0]
+
+
+def _ld_supported(g):
+    if g.scheme != 0 or g.theta_mode != 0:
+        raise ValueError("the extended-precision oracle covers WENO5 with centred theta only")
+
+
+def ld_rhs(g, coef, u):
+    _ld_supported(g)
+    coef, u = _f64(coef), _ld(u)
+    F = np.zeros(u.shape, dtype=np.longdouble)
+    _load_ld().orc_ld_rhs(ctypes.byref(g), _ptr(coef), _ptr(u), _ptr(F))
+    return F
+
+
+def ld_rk3_step(g, coef, dt, u, nsteps=1):
+    _ld_supported(g)
+    coef = _f64(coef)
+    u = _ld(u).copy()
+    _load_ld().orc_ld_rk3_step(ctypes.byref(g), _ptr(coef), float(dt), _ptr(u), int(nsteps))
+    return u

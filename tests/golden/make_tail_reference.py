@@ -11,8 +11,14 @@ a = 0 (and away from the horizon at a = M). The pulse's reflection from the
 outer end (r* = 5000 M) returns to r* = 50 M at t ~ 9900 M, so the tail is read
 before that.
 
+With --ld the state, weights and fluxes are carried in C long double by the
+extended-precision oracle instead (same grid, coefficients, time step and
+initial data), written to tail_coarse_reference_ld.txt: the difference of the
+two files is the binary64 state's own round-off along the tail.
+
 Calls only the oracle and the seeded inputs:
     python tests/golden/make_tail_reference.py        # about 10 min on 8 cores
+    python tests/golden/make_tail_reference.py --ld   # about 20 min on 8 cores
 """
 import os
 import sys
@@ -44,11 +50,14 @@ def time_step(g, co):
     return EVERY / n, n
 
 
-def run(a):
+def run(a, ld=False):
     wl = coarse_workload(a)
     g = o.grid(NR, NTH, wl.rs_min, wl.rs_max, 1.0, a, 0, 0)
     co = o.coefficients(g)
     u = I.initial_data(wl)
+    if ld:
+        u = u.astype(np.longdouble)
+    step = o.ld_rk3_step if ld else o.rk3_step
     h = (wl.rs_max - wl.rs_min) / (NR - 1)
     ie = int(round((R_EXT - wl.rs_min) / h))
     DT, n = time_step(g, co)
@@ -56,32 +65,46 @@ def run(a):
     ts, ys = [], []
     t = 0.0
     while t < T_END - 1e-9:
-        u = o.rk3_step(g, co, DT, u, n)
+        u = step(g, co, DT, u, n)
         t += n * DT
         ts.append(t)
         ys.append(u[0, NTH // 2, ie])
         print(f"a={a} t={t:.0f}", flush=True)
-    ts, ys = np.array(ts), np.array(ys)
+    ts, ys = np.array(ts), np.array(ys, dtype=u.dtype)
     p = np.full_like(ts, np.nan)
     p[1:-1] = ts[1:-1] * (ys[2:] - ys[:-2]) / (ts[2:] - ts[:-2]) / ys[1:-1]
     return ts, ys, p
 
 
 def main():
+    ld = "--ld" in sys.argv[1:]
     rows = []
     for a in (0.0, 1.0):
-        ts, ys, p = run(a)
+        ts, ys, p = run(a, ld)
         rows += [(a, t, y, q) for t, y, q in zip(ts, ys, p)]
-    out = os.path.join(HERE, "tail_coarse_reference.txt")
+    out = os.path.join(HERE, "tail_coarse_reference_ld.txt" if ld else "tail_coarse_reference.txt")
     with open(out, "w") as fh:
-        fh.write("# Oracle reference (binary64 weights, SSP-RK(3,3), stability-rule dt) for\n"
-                 "# the tail workload coarsened to 4096 x 8 (r* in [-5000, 5000] M, s = m = 0,\n"
-                 "# l = 0 pulse at 50 M): Psi at r* = 50 M, theta row 4, every 100 M, and the\n"
-                 "# local index p = t dPsi/dt / Psi. Written by\n"
-                 "# tests/golden/make_tail_reference.py (oracle and seeded inputs only).\n"
-                 "# columns: a  t  Psi  p\n")
-        for a, t, y, q in rows:
-            fh.write(f"{a:.1f} {t:.1f} {y:.17e} {q:.10f}\n")
+        if ld:
+            fh.write("# Extended-precision oracle reference (state, weights and fluxes in C long\n"
+                     f"# double, {o.ld_mant_dig()}-bit significand; SSP-RK(3,3), stability-rule dt)\n"
+                     "# for the tail workload coarsened to 4096 x 8 (r* in [-5000, 5000] M,\n"
+                     "# s = m = 0, l = 0 pulse at 50 M): Psi at r* = 50 M, theta row 4, every\n"
+                     "# 100 M, and the local index p = t dPsi/dt / Psi. Written by\n"
+                     "# tests/golden/make_tail_reference.py --ld (oracle and seeded inputs only).\n"
+                     "# columns: a  t  Psi  p\n")
+            for a, t, y, q in rows:
+                fh.write(f"{a:.1f} {t:.1f} "
+                         f"{np.format_float_scientific(y, precision=20, unique=False)} "
+                         f"{float(q):.10f}\n")
+        else:
+            fh.write("# Oracle reference (binary64 weights, SSP-RK(3,3), stability-rule dt) for\n"
+                     "# the tail workload coarsened to 4096 x 8 (r* in [-5000, 5000] M, s = m = 0,\n"
+                     "# l = 0 pulse at 50 M): Psi at r* = 50 M, theta row 4, every 100 M, and the\n"
+                     "# local index p = t dPsi/dt / Psi. Written by\n"
+                     "# tests/golden/make_tail_reference.py (oracle and seeded inputs only).\n"
+                     "# columns: a  t  Psi  p\n")
+            for a, t, y, q in rows:
+                fh.write(f"{a:.1f} {t:.1f} {y:.17e} {q:.10f}\n")
     print("wrote", out)
 
 

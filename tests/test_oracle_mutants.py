@@ -5,7 +5,10 @@ operands), compiles the copy, and runs the oracle's pins against it (through
 TEUK_ORACLE_LIB). Every planted mistake must make at least one pin fail, and
 the unaltered copy must pass the same pins, so that the pins tie every part of
 the oracle to the paper and to the mathematics rather than to itself.
-The pins each mistake is run against are listed beside it."""
+The pins each mistake is run against are listed beside it. LD_MUTANTS do the
+same for the extended-precision oracle (oracle/teuk_oracle_ld.c, loaded
+through TEUK_ORACLE_LD_LIB), including slips that would quietly drop its
+extra precision."""
 import concurrent.futures as cf
 import os
 import subprocess
@@ -17,6 +20,7 @@ import oracle as o
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "teuk_oracle.c")
+SRC_LD = os.path.join(ROOT, "oracle", "teuk_oracle_ld.c")
 
 P = "tests/test_oracle_pins.py::"
 PH = "tests/test_oracle_physics.py::"
@@ -230,8 +234,50 @@ MUTANTS = [
 ]
 
 
-def _run_pins(lib_path, pins):
-    env = dict(os.environ, TEUK_ORACLE_LIB=lib_path, OMP_NUM_THREADS="2")
+LD = "tests/test_oracle_ld.py::"
+LD_FLUX = LD + "test_flux_of_linear_data_in_closed_form"
+LD_LIN = LD + "test_rhs_of_linear_state_in_closed_form"
+LD_RHS = LD + "test_rhs_agrees_with_binary64_oracle"
+LD_EVO = LD + "test_evolution_agrees_with_binary64_oracle"
+LD_PREC = LD + "test_evolution_carries_the_extended_precision"
+
+LD_MUTANTS = [
+    ("ld: candidate value q1 over 5", "q[1] = (-g[1] + 5 * g[2] + 2 * g[3]) / 6.0L;",
+     "q[1] = (-g[1] + 5 * g[2] + 2 * g[3]) / 5.0L;", [LD_FLUX]),
+    ("ld: q2 with g3 and g4 swapped", "q[2] = (2 * g[2] + 5 * g[3] - g[4]) / 6.0L;",
+     "q[2] = (2 * g[2] + 5 * g[4] - g[3]) / 6.0L;", [LD_FLUX]),
+    ("ld: linear weights reversed", "const real d[3] = {0.1L, 0.6L, 0.3L};",
+     "const real d[3] = {0.3L, 0.6L, 0.1L};", [LD_RHS]),
+    ("ld: IS0 second term 3 -> 2", "t = g[0] - 4 * g[1] + 3 * g[2];",
+     "t = g[0] - 4 * g[1] + 2 * g[2];", [LD_RHS]),
+    ("ld: alpha with the first power", "alpha[k] = d[k] / (e * e);",
+     "alpha[k] = d[k] / e;", [LD_RHS]),
+    ("ld: negative-direction stencil one node left", "dir > 0 ? &ext[i + 1] : &ext[i + 2]",
+     "dir > 0 ? &ext[i + 1] : &ext[i + 1]", [LD_LIN, LD_RHS]),
+    ("ld: quartic ghost through the wrong nodes", "const int x0 = k < 0 ? 0 : n - 5;",
+     "const int x0 = k < 0 ? 0 : n - 6;", [LD_RHS]),
+    ("ld: sign of b D_Psi", "const creal_t Fpsi = pi - b * Dpsi;",
+     "const creal_t Fpsi = pi + b * Dpsi;", [LD_LIN, LD_RHS]),
+    ("ld: C multiplies pi", "+ Bt * pi + C * psi;", "+ Bt * pi + C * pi;", [LD_LIN, LD_RHS]),
+    ("ld: sign of the theta first derivative",
+     "(nb[0] - 8 * nb[1] + 8 * nb[3] - nb[4]) / (12 * dth)",
+     "(nb[4] - 8 * nb[3] + 8 * nb[1] - nb[0]) / (12 * dth)", [LD_RHS]),
+    ("ld: pole mirror off by one", "if (jj < 0) { jj = -1 - jj; s = sigma; }",
+     "if (jj < 0) { jj = -jj; s = sigma; }", [LD_RHS]),
+    ("ld: stage 2 combines u1 for u", "u2[k] = 0.75L * u[k] + 0.25L * (u1[k] + dt * Fv[k]);",
+     "u2[k] = 0.75L * u1[k] + 0.25L * (u1[k] + dt * Fv[k]);", [LD_EVO]),
+    ("ld: stage 1 through binary64", "u1[k] = u[k] + dt * Fv[k];",
+     "u1[k] = (double)u[k] + dt * Fv[k];", [LD_PREC]),
+    ("ld: stage 3 through binary64", "u[k] = u[k] / 3 + 2 * (u2[k] + dt * Fv[k]) / 3;",
+     "u[k] = (double)(u[k] / 3 + 2 * (u2[k] + dt * Fv[k]) / 3);", [LD_PREC]),
+    ("ld: flux accumulated in binary64", "real fh = 0.0L;", "double fh = 0.0L;",
+     [LD_FLUX, LD_LIN]),
+]
+
+
+def _run_pins(lib_path, pins, var="TEUK_ORACLE_LIB"):
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    env[var] = lib_path
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
            *pins]
     out = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
@@ -272,5 +318,40 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
         results = list(ex.map(job, range(len(jobs))))
     rc0, log0 = results[0]
     assert rc0 == 0, "the unaltered oracle fails its pins:\n" + log0
+    survivors = [(j[0], rc, log) for j, (rc, log) in zip(jobs[1:], results[1:]) if rc != 1]
+    assert not survivors, "\n\n".join(f"{n}: pytest exit {rc}\n{log}" for n, rc, log in survivors)
+
+
+def test_ld_mutants_are_distinct_single_edits():
+    text = open(SRC_LD).read()
+    names = [m[0] for m in LD_MUTANTS]
+    assert len(set(names)) == len(names)
+    for name, old, new, pins in LD_MUTANTS:
+        assert text.count(old) == 1, name
+        assert old != new and pins, name
+
+
+@pytest.mark.slow
+def test_every_planted_ld_mistake_fails_a_pin(tmp_path):
+    text = open(SRC_LD).read()
+    tmp = str(tmp_path)
+    all_pins = sorted({p for m in LD_MUTANTS for p in m[3]})
+    jobs = [("original", text, all_pins)]
+    for name, old, new, pins in LD_MUTANTS:
+        jobs.append((name, text.replace(old, new), pins))
+
+    def job(k):
+        _, mutated, pins = jobs[k]
+        src = os.path.join(tmp, f"oracle_ld_{k}.c")
+        with open(src, "w") as fh:
+            fh.write(mutated)
+        lib = o.build_ld(force=True, src=src, out=os.path.join(tmp, f"liboracle_ld_{k}.so"))
+        return _run_pins(lib, pins, "TEUK_ORACLE_LD_LIB")
+
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(job, range(len(jobs))))
+    rc0, log0 = results[0]
+    assert rc0 == 0, "the unaltered extended oracle fails its pins:\n" + log0
     survivors = [(j[0], rc, log) for j, (rc, log) in zip(jobs[1:], results[1:]) if rc != 1]
     assert not survivors, "\n\n".join(f"{n}: pytest exit {rc}\n{log}" for n, rc, log in survivors)
