@@ -41,7 +41,8 @@ static int scratch_states(const teuk_params& p) { return p.rk == TEUK_RK_SSP104 
 
 // One step of p's integrator (Sec. 3.2) in place on u; w holds
 // scratch_states(p) arrays of 4 planes.
-//   SSP-RK(3,3): u -> w1 -> w2 -> u.
+//   SSP-RK(3,3): u -> w1 -> w2 -> u (with WENO5, w2 = 4 u^(2): the scaled
+//   second stage of teuk_stage_kernels.cuh).
 //   SSP-RK(10,4): stages 1-5 are forward-Euler steps of dt/6 from u (A/B
 //   ping-pong), then q = u/25 + 9/25 u5' and u5 = 3/5 u + 2/5 u5' (u5' the fifth
 //   forward-Euler result), stages 6-9 forward Euler from u5, and
@@ -75,8 +76,17 @@ static cudaError_t launch_step(const teuk_params& p, const double* coef, double 
         return e;
     }
     e = launch_stage(p, coef, nullptr, u, w, 1, dt, st);
-    if (e == cudaSuccess) e = launch_stage(p, coef, u, w, w + n, 2, dt, st);
-    if (e == cudaSuccess) e = launch_stage(p, coef, u, w + n, u, 3, dt, st);
+    if (p.scheme == TEUK_SCHEME_FD6_KO8) {
+        if (e == cudaSuccess) e = launch_stage(p, coef, u, w, w + n, 2, dt, st);
+        if (e == cudaSuccess) e = launch_stage(p, coef, u, w + n, u, 3, dt, st);
+        return e;
+    }
+    // WENO5: w2 holds 4 u^(2), and the third stage runs on it with 16 eps
+    // (teuk_stage_kernels.cuh, kStageScaled)
+    if (e == cudaSuccess)
+        e = launch_stage_ab(p, coef, u, w, w + n, kStageScaled, dt, 3.0, 1.0, st);
+    if (e == cudaSuccess)
+        e = launch_stage_ab(p, coef, u, w + n, u, 3, dt, 1.0 / 3.0, 1.0 / 6.0, st, 4);
     return e;
 }
 

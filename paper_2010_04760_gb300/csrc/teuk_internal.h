@@ -89,9 +89,13 @@ size_t batch_desc_bytes(int n);
 #ifdef __CUDACC__
 #include <cuda_runtime.h>
 namespace teuk {
+// kind 4 (kStageScaled): u_out = alpha u_n + u_prev + h F(u_prev), the scaled
+// second stage of the WENO5 SSP-RK(3,3) step; eps_log2 scales the WENO
+// epsilon by 2^eps_log2 (4 for the stage after it).
+constexpr int kStageScaled = 4;
 cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const double* un,
                             const double* up, double* out, int kind, double h, double alpha,
-                            double beta, cudaStream_t st);
+                            double beta, cudaStream_t st, int eps_log2 = 0);
 cudaError_t launch_rk104_combine(const double* u, const double* v, double* q, double* u5,
                                  long long n, cudaStream_t st);
 cudaError_t upload_batch_desc(const BatchEvo* evos, int n, int segv, void* d_desc,

@@ -4,6 +4,8 @@
 // teuk_stage_hyp.cu.
 #include "teuk_stage_kernels.cuh"
 
+#include <cmath>
+
 namespace teuk {
 
 // eps = m 2^E with m in [1, 2): E, whether m == 1, and the binary32 bits of m
@@ -60,18 +62,23 @@ cudaError_t launch_stage(const teuk_params& p, const double* coef, const double*
 }
 
 // kind 0: u_out = h F(u_prev); kind 1: u_out = u_prev + h F(u_prev);
-// kind >= 2: u_out = alpha u_n + beta (u_prev + h F(u_prev)).
+// kind 2, 3: u_out = alpha u_n + beta (u_prev + h F(u_prev));
+// kind kStageScaled (WENO5 only): u_out = alpha u_n + u_prev + h F(u_prev).
+// eps_log2: the WENO epsilon times 2^eps_log2.
 cudaError_t launch_stage_ab(const teuk_params& p, const double* coef, const double* un,
                             const double* up, double* out, int kind, double h, double alpha,
-                            double beta, cudaStream_t st) {
-    const int stage = kind > 2 ? 2 : kind;
+                            double beta, cudaStream_t st, int eps_log2) {
+    const int stage = kind == kStageScaled ? kStageScaled : (kind > 2 ? 2 : kind);
     StageArgs A;
     stage_args_common(A, p);
     A.coef = coef; A.un = un; A.up = up; A.out = out;
     A.dt = h;
     A.alpha = alpha;
     A.beta = beta;
+    A.eps4 = std::ldexp(A.eps4, eps_log2);
+    A.eps_exp += eps_log2;
     if (p.scheme == TEUK_SCHEME_FD6_KO8) {
+        if (stage == kStageScaled) return cudaErrorInvalidValue;
         A.ko = h * p.ko_sigma / (256.0 * ((p.rstar_max - p.rstar_min) / (p.nr - 1)));
         dim3 grid((A.nr + 31) / 32, (A.nth + WARPS - 1) / WARPS), block(WARPS * 32);
         if (p.coords == TEUK_COORDS_HYPERBOLOIDAL) {

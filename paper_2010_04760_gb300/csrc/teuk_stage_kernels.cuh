@@ -87,6 +87,25 @@ struct StageArgs {
     double ko;            // FD6+KO8 scheme: h_stage sigma / (256 h), else 0
 };
 
+// The SSP-RK(3,3) step of the WENO5 scheme keeps its second stage scaled by
+// four (Sec. 3.2): v = 4 u^(2) = 3 u^n + (u^(1) + dt F(u^(1))), one
+// multiply-add per row fewer than 3/4 u^n + 1/4 (...) (the kStageScaled form
+// of the stage kernels, alpha = 3). The third stage then needs F(v/4). The
+// smoothness indicators are quadratic in the data, so data scaled by 4 and
+// epsilon scaled by 16 give every (eps + IS_k) times 16 and the same weights
+// (Sec. 3.1.2), while the rest of F is linear: F_eps(v/4) = F_16eps(v)/4, and
+// u^{n+1} = 1/3 u^n + 1/6 (v + dt F_16eps(v)). Scaling by powers of two is
+// exact in binary floating point and commutes with every rounding, so this
+// third stage rounds exactly like 1/3 u^n + 2/3 (u^(2) + dt F(u^(2))) on
+// u^(2) = v/4; only the second stage's own roundings differ (one fewer).
+constexpr double kScaledAlpha = 3.0;
+constexpr double kThirdBetaScaled = 1.0 / 6.0;
+constexpr int kScaledEpsLog2 = 4;      // the third stage's eps: 16 eps
+__host__ __device__ inline void eps_times_16(StageArgs& A) {
+    A.eps4 *= 16.0;
+    A.eps_exp += kScaledEpsLog2;
+}
+
 // ---------------------------------------------------------------------------
 // Exact bit-level helpers (integer pipes only).
 // ---------------------------------------------------------------------------
@@ -446,6 +465,17 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     double acc0, acc1, acc2, acc3;
     if (STAGE == 0) {
         acc0 = A.dt * pir; acc1 = A.dt * pii; acc2 = 0.0; acc3 = 0.0;
+    } else if (STAGE == kStageScaled) {
+        // alpha u^n + u_prev + dt F(u_prev): u^n enters through the first
+        // multiply-add of each row, and no combination is left for the end
+        const double* un = A.un + q;
+        const double n0 = FUSED ? __ldcg(un) : un[0], n1 = FUSED ? __ldcg(un + P) : un[P];
+        const double n2 = FUSED ? __ldcg(un + 2 * P) : un[2 * P];
+        const double n3 = FUSED ? __ldcg(un + 3 * P) : un[3 * P];
+        acc0 = fma(A.dt, pir, fma(A.alpha, n0, psr));
+        acc1 = fma(A.dt, pii, fma(A.alpha, n1, psi));
+        acc2 = fma(A.alpha, n2, pir);
+        acc3 = fma(A.alpha, n3, pii);
     } else {
         acc0 = fma(A.dt, pir, psr); acc1 = fma(A.dt, pii, psi); acc2 = pir; acc3 = pii;
     }
@@ -500,7 +530,7 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
         acc2 = fma(-A.ko, E2, acc2);
         acc3 = fma(-A.ko, E3, acc3);
     }
-    if (STAGE >= 2) {
+    if (STAGE == 2 || STAGE == 3) {
         const double* un = A.un + q;
         const double n0 = FUSED ? __ldcg(un) : un[0], n1 = FUSED ? __ldcg(un + P) : un[P];
         const double n2 = FUSED ? __ldcg(un + 2 * P) : un[2 * P];
@@ -661,10 +691,15 @@ __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, 
             A.ko = 0.0;
             double* w1 = d.w;
             double* w2 = d.w + 4 * d.plane;
+            // the step's second stage in its scaled form (kStageScaled)
             if (STAGE == 1) { A.un = nullptr; A.up = d.u; A.out = w1; A.alpha = 0.0; A.beta = 1.0; }
-            if (STAGE == 2) { A.un = d.u; A.up = w1; A.out = w2; A.alpha = 0.75; A.beta = 0.25; }
-            if (STAGE == 3) { A.un = d.u; A.up = w2; A.out = d.u; A.alpha = 1.0 / 3.0; A.beta = 2.0 / 3.0; }
-            process_segment<W, STAGE, THETA, SEGV, 0, HYP>(A, sm[warp], lane, j, seg_blk);
+            if (STAGE == 2) { A.un = d.u; A.up = w1; A.out = w2; A.alpha = kScaledAlpha; A.beta = 1.0; }
+            if (STAGE == 3) {
+                A.un = d.u; A.up = w2; A.out = d.u; A.alpha = 1.0 / 3.0; A.beta = kThirdBetaScaled;
+                eps_times_16(A);
+            }
+            process_segment<W, STAGE == 2 ? kStageScaled : STAGE, THETA, SEGV, 0, HYP>(
+                A, sm[warp], lane, j, seg_blk);
         }
         __syncwarp();
     }
@@ -712,8 +747,9 @@ cudaError_t launch_stage_wt(const StageArgs& A, int stage, cudaStream_t st) {
     switch (stage) {
     case 0: return launch_early(stage_kernel<W, 0, THETA, HYP>, grid, block, A, st);
     case 1: return launch_early(stage_kernel<W, 1, THETA, HYP>, grid, block, A, st);
-    case 2: return launch_early(stage_kernel<W, 2, THETA, HYP>, grid, block, A, st);
-    default: return launch_early(stage_kernel<W, 3, THETA, HYP>, grid, block, A, st);
+    case kStageScaled:
+        return launch_early(stage_kernel<W, kStageScaled, THETA, HYP>, grid, block, A, st);
+    default: return launch_early(stage_kernel<W, 2, THETA, HYP>, grid, block, A, st);
     }
 }
 
@@ -882,15 +918,21 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
         if (!s_go) break;
         const int stage = e % 3 + 1;
         StageArgs A = F.A;
+        // the second stage in its scaled form (kStageScaled), as in the stage launches
         if (stage == 1) { A.un = nullptr; A.up = F.u; A.out = F.w1; A.alpha = 0.0; A.beta = 1.0; }
-        if (stage == 2) { A.un = F.u; A.up = F.w1; A.out = F.w2; A.alpha = 0.75; A.beta = 0.25; }
+        if (stage == 2) { A.un = F.u; A.up = F.w1; A.out = F.w2; A.alpha = kScaledAlpha; A.beta = 1.0; }
         if (stage == 3) {
-            A.un = F.u; A.up = F.w2; A.out = F.u; A.alpha = 1.0 / 3.0; A.beta = 2.0 / 3.0;
+            A.un = F.u; A.up = F.w2; A.out = F.u; A.alpha = 1.0 / 3.0; A.beta = kThirdBetaScaled;
+            eps_times_16(A);
         }
         const int j = rb * WARPS + warp;
         if (j < A.nth) {
-            if (stage == 1) process_segment<W, 1, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
-            else process_segment<W, 2, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
+            if (stage == 1)
+                process_segment<W, 1, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
+            else if (stage == 2)
+                process_segment<W, kStageScaled, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
+            else
+                process_segment<W, 2, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
         }
         __syncthreads();            // every row's stores of this item are issued
         if (threadIdx.x == 0 && !(F.withhold && e == 0 && item == 0)) {
