@@ -49,10 +49,10 @@ BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # sources it was taken on, identified by the sha256 of their concatenation.
 NCU_TRAFFIC = {"sources": ["paper_2010_04760_gb300/csrc/teuk_stage_kernels.cuh",
                            "paper_2010_04760_gb300/csrc/teuk_stage.cu"],
-               "sha256": "b9951a056a0df4d53c0f5d7216217d149918c13f2ff6c82834f545a739dc1074",
+               "sha256": "b10c765236c55e79c88bd79de5ec4b9eea810958ee7f993e613b225d10e1d781",
                "bytes_per_launch": None,
-               "fused_bytes_per_launch": (31520000 + 3328 + 31518976 + 8704 + 31519744
-                                          + 5120) / 3.0}
+               "fused_bytes_per_launch": (31525888 + 5632 + 31525120 + 3072 + 31524608
+                                          + 15360) / 3.0}
 
 
 def workload_config(wl, wprec):

@@ -543,56 +543,38 @@ __device__ __forceinline__ void node_update(const StageArgs& A, const double* sw
     out[0] = acc0; out[1] = acc1; out[2] = acc2; out[3] = acc3;
 }
 
-// One warp's work: segment seg_blk (nodes seg_blk*SEG ..) of theta row j of
-// the evolution described by A. sw is the warp's shared-memory block.
-template <int W, int STAGE, int THETA, int SEGV, int SCHEME = 0, bool HYP = false,
-          bool FUSED = false>
-__device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, int lane, int j,
-                                                int seg_blk) {
-    using G = std::conditional_t<SCHEME == 1, GeoFD<SEGV>, Geo<SEGV>>;
-    constexpr int SEG = G::SEG, ND = G::ND, NS = G::NS, NF = G::NF, NW = G::NW;
-    constexpr int HALO = SCHEME == 1 ? 4 : 3;
+// Phase 1 at one flat index of a warp's segment: the first difference
+// d_k (component c, k = i0-HALO ..) of row `row` into the warp's block sw
+// (ghosts: edge copies, d = 0; on the hyperboloidal slices the quartic
+// through the five edge nodes).
+template <int HALO, int ND, int NW, bool HYP, bool FUSED>
+__device__ __forceinline__ void first_difference(const StageArgs& A, double* sw, long long row,
+                                                 int i0, int c, int k) {
     const int nr = A.nr;
-    const int i0 = seg_blk * SEG;
-    const long long row = (long long)j * nr;
-#define DL(c, k) sw[(c) * NW + (k)]
-#define SD(c, k) sw[(c) * NW + ND + (k)]
-#define FL(c, k) sw[(c) * NW + ND + NS + (k)]
+    const int g = i0 - HALO + k;
+    const double* f = A.up + c * A.plane + row;
+    double v;
+    if (HYP && (g < 0 || g >= nr - 1)) {
+        // nodes beyond nr-1+HALO feed no stored node
+        v = g + 1 <= nr - 1 + HALO
+                ? ghost_value<FUSED>(f, nr, g + 1) - ghost_value<FUSED>(f, nr, g)
+                : 0.0;
+    } else {
+        const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
+        v = ld_state<FUSED>(f + ib) - ld_state<FUSED>(f + ia);
+    }
+    sw[c * NW + k] = v;
+}
 
-    // 1. first differences d_k, k = i0-HALO .. (ghosts: edge copies, d = 0;
-    //    on the hyperboloidal slices the quartic through the five edge nodes)
-    for (int idx = lane; idx < 4 * ND; idx += 32) {
-        const int c = idx / ND, k = idx - c * ND;
-        const int g = i0 - HALO + k;
-        const double* f = A.up + c * A.plane + row;
-        if (HYP && (g < 0 || g >= nr - 1)) {
-            // nodes beyond nr-1+HALO feed no stored node
-            DL(c, k) = g + 1 <= nr - 1 + HALO
-                           ? ghost_value<FUSED>(f, nr, g + 1) - ghost_value<FUSED>(f, nr, g)
-                           : 0.0;
-        } else {
-            const int ia = min(max(g, 0), nr - 1), ib = min(max(g + 1, 0), nr - 1);
-            DL(c, k) = ld_state<FUSED>(f + ib) - ld_state<FUSED>(f + ia);
-        }
-    }
-    __syncwarp();
-    if constexpr (SCHEME == 0) {
-    // 2. s_k = d_{k-1} - 2 d_k + d_{k+1}, k = i0-2 .. i0+SEG
-    for (int idx = lane; idx < 4 * NS; idx += 32) {
-        const int c = idx / NS, k = idx - c * NS;
-        SD(c, k) = fma(-2.0, DL(c, k + 1), DL(c, k) + DL(c, k + 2));
-    }
-    __syncwarp();
-    // 3. interface flux terms, i + 1/2 for i = i0-1 .. i0+SEG-1
-    for (int idx = lane; idx < 4 * NF; idx += 32) {
-        const int c = idx / NF;
-        FL(c, idx - c * NF) = interface_flux<W, G>(sw, idx, A);
-    }
-    __syncwarp();
-    }
-    // 4. nodes i = i0 .. i0+SEG-1 (two per lane and iteration, computed side
-    //    by side; the second node's loads use a clamped index and its store is
-    //    predicated)
+// Phase 4: nodes i = i0 .. i0+SEG-1 of row j (two per lane and iteration
+// when SEG = 64, computed side by side; the second node's loads use a clamped
+// index and its store is predicated).
+template <int W, int STAGE, int THETA, class G, int SCHEME, bool HYP, bool FUSED>
+__device__ __forceinline__ void node_phase(const StageArgs& A, const double* sw, int lane, int j,
+                                           int i0) {
+    constexpr int SEG = G::SEG;
+    const int nr = A.nr;
+    const long long row = (long long)j * nr;
     for (int p = lane; p < SEG; p += 64) {
         double ua[4], ub[4];
         node_update<W, STAGE, THETA, G, SCHEME, HYP, FUSED>(A, sw, j, i0, p, ua);
@@ -608,9 +590,68 @@ __device__ __forceinline__ void process_segment(const StageArgs& A, double* sw, 
             A.out[q] = ub[0]; A.out[P + q] = ub[1]; A.out[2 * P + q] = ub[2]; A.out[3 * P + q] = ub[3];
         }
     }
-#undef DL
-#undef SD
-#undef FL
+}
+
+// One warp's work (the FD6 + KO8 scheme): segment seg_blk (nodes
+// seg_blk*SEG ..) of theta row j; sw is the warp's shared-memory block. The
+// scheme needs only the first differences (4 x (SEG + 8) of them, whole
+// 32-lane iterations).
+template <int STAGE, int SEGV, bool HYP>
+__device__ __forceinline__ void process_segment_fd6(const StageArgs& A, double* sw, int lane, int j,
+                                                    int seg_blk) {
+    using G = GeoFD<SEGV>;
+    constexpr int ND = G::ND, NW = G::NW;
+    const int i0 = seg_blk * G::SEG;
+    const long long row = (long long)j * A.nr;
+    for (int idx = lane; idx < 4 * ND; idx += 32) {
+        const int c = idx / ND;
+        first_difference<4, ND, NW, HYP, false>(A, sw, row, i0, c, idx - c * ND);
+    }
+    __syncwarp();
+    node_phase<TEUK_W_FP64, STAGE, TEUK_THETA_CENTERED4, G, 1, HYP, false>(A, sw, lane, j, i0);
+}
+
+// One work item of the WENO5 scheme: radial segment seg_blk of the rows
+// j0 .. j0+nrows-1 (nrows <= WARPS; warp w owns row j0 + w and the block
+// sm + w * 4 NW of shared memory). The three halo phases (first differences,
+// third differences s_k = d_{k-1} - 2 d_k + d_{k+1}, interface flux terms)
+// are shared by all threads of the block as one flat list per phase over
+// the item's rows, so that only the block's last 32-lane iteration of a
+// phase can leave lanes idle (a warp doing its own row alone idles 12, 20
+// and 28 lanes of its last iterations on 32-node segments). Every thread of
+// the block must call this (it contains block barriers); the node phase is
+// the warp's own.
+template <int W, int STAGE, int THETA, int SEGV, bool HYP = false, bool FUSED = false>
+__device__ __forceinline__ void process_item(const StageArgs& A, double* sm, int j0, int nrows,
+                                             int seg_blk) {
+    using G = Geo<SEGV>;
+    constexpr int ND = G::ND, NS = G::NS, NF = G::NF, NW = G::NW;
+    const int i0 = seg_blk * G::SEG;
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    for (int idx = t; idx < nrows * 4 * ND; idx += WARPS * 32) {
+        const int r = idx / (4 * ND), e = idx - r * (4 * ND);
+        const int c = e / ND;
+        first_difference<3, ND, NW, HYP, FUSED>(A, sm + r * (4 * NW), (long long)(j0 + r) * A.nr,
+                                                i0, c, e - c * ND);
+    }
+    __syncthreads();
+    for (int idx = t; idx < nrows * 4 * NS; idx += WARPS * 32) {
+        const int r = idx / (4 * NS), e = idx - r * (4 * NS);
+        const int c = e / NS, k = e - c * NS;
+        const double* dl = sm + r * (4 * NW) + c * NW;
+        sm[r * (4 * NW) + c * NW + ND + k] = fma(-2.0, dl[k + 1], dl[k] + dl[k + 2]);
+    }
+    __syncthreads();
+    for (int idx = t; idx < nrows * 4 * NF; idx += WARPS * 32) {
+        const int r = idx / (4 * NF), e = idx - r * (4 * NF);
+        const int c = e / NF;
+        double* sw = sm + r * (4 * NW);
+        sw[c * NW + ND + NS + (e - c * NF)] = interface_flux<W, G>(sw, e, A);
+    }
+    __syncthreads();
+    if (warp < nrows)
+        node_phase<W, STAGE, THETA, G, 0, HYP, FUSED>(A, sm + warp * (4 * NW), lane, j0 + warp, i0);
 }
 
 // Programmatic dependent launch (PTX griddepcontrol, sm_90 and later): the
@@ -629,10 +670,8 @@ __global__ void TEUK_BOUNDS stage_kernel(const StageArgs A) {
     constexpr int SEGV = Seg<W>::value;
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
     dependent_launch_gate();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.y * WARPS + warp;
-    if (j >= A.nth) return;
-    process_segment<W, STAGE, THETA, SEGV, 0, HYP>(A, sm[warp], lane, j, blockIdx.x);
+    const int j0 = blockIdx.y * WARPS;
+    process_item<W, STAGE, THETA, SEGV, HYP>(A, &sm[0][0], j0, min(WARPS, A.nth - j0), blockIdx.x);
 }
 
 // FD6 + KO8 comparison scheme (Sec. 3.1.1), single evolution, centred theta;
@@ -645,8 +684,7 @@ __global__ void TEUK_BOUNDS fd6_stage_kernel(const StageArgs A) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.y * WARPS + warp;
     if (j >= A.nth) return;
-    process_segment<TEUK_W_FP64, STAGE, TEUK_THETA_CENTERED4, SEGV, 1, HYP>(A, sm[warp], lane, j,
-                                                                           blockIdx.x);
+    process_segment_fd6<STAGE, SEGV, HYP>(A, sm[warp], lane, j, blockIdx.x);
 }
 
 // Batched evolutions: one work item is a block of WARPS rows x one segment of
@@ -670,7 +708,6 @@ template <int W, int STAGE, int THETA, int SEGV, bool HYP = false>
 __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, int n,
                                                long long items) {
     __shared__ double sm[WARPS][4 * Geo<SEGV>::NW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // The member of item `it` is the last k with item0 <= it. A block's items
     // rise, so its member index only moves forward: usually zero or one load
     // per item instead of a binary search (measured: 2% faster on 64 members).
@@ -680,8 +717,8 @@ __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, 
         const BatchDesc& d = D[lo];
         const long long local = it - d.item0;
         const int seg_blk = (int)(local % d.nseg);
-        const int j = (int)(local / d.nseg) * WARPS + warp;
-        if (j < d.nth) {
+        const int j0 = (int)(local / d.nseg) * WARPS;
+        {
             StageArgs A;
             A.coef = d.coef;
             A.nr = d.nr; A.nth = d.nth; A.plane = d.plane;
@@ -698,10 +735,10 @@ __global__ void TEUK_BOUNDS batch_stage_kernel(const BatchDesc* __restrict__ D, 
                 A.un = d.u; A.up = w2; A.out = d.u; A.alpha = 1.0 / 3.0; A.beta = kThirdBetaScaled;
                 eps_times_16(A);
             }
-            process_segment<W, STAGE == 2 ? kStageScaled : STAGE, THETA, SEGV, 0, HYP>(
-                A, sm[warp], lane, j, seg_blk);
+            process_item<W, STAGE == 2 ? kStageScaled : STAGE, THETA, SEGV, HYP>(
+                A, &sm[0][0], j0, min(WARPS, d.nth - j0), seg_blk);
         }
-        __syncwarp();
+        __syncthreads();            // the next item's halo phases overwrite sm
     }
 }
 
@@ -925,15 +962,13 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
             A.un = F.u; A.up = F.w2; A.out = F.u; A.alpha = 1.0 / 3.0; A.beta = kThirdBetaScaled;
             eps_times_16(A);
         }
-        const int j = rb * WARPS + warp;
-        if (j < A.nth) {
-            if (stage == 1)
-                process_segment<W, 1, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
-            else if (stage == 2)
-                process_segment<W, kStageScaled, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
-            else
-                process_segment<W, 2, THETA, SEGV, 0, HYP, true>(A, sm[warp], lane, j, sg);
-        }
+        const int j0 = rb * WARPS, nrows = min(WARPS, A.nth - j0);
+        if (stage == 1)
+            process_item<W, 1, THETA, SEGV, HYP, true>(A, &sm[0][0], j0, nrows, sg);
+        else if (stage == 2)
+            process_item<W, kStageScaled, THETA, SEGV, HYP, true>(A, &sm[0][0], j0, nrows, sg);
+        else
+            process_item<W, 2, THETA, SEGV, HYP, true>(A, &sm[0][0], j0, nrows, sg);
         __syncthreads();            // every row's stores of this item are issued
         if (threadIdx.x == 0 && !(F.withhold && e == 0 && item == 0)) {
             __threadfence();
