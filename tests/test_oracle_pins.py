@@ -378,3 +378,31 @@ def test_ko8_annihilates_degree_seven_and_has_its_fourier_symbol():
         _, Q = o.fd6_ko8_1d(f, h, sigma)
         symbol = sigma * (2.0 * np.sin(np.pi * k * h)) ** 8 / (256.0 * h)
         assert np.max(np.abs(Q - symbol * f)) < 1e-12 * max(1.0, symbol)
+
+
+@pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("coords", [0, 1])
+def test_weno_operator_homogeneous_with_scaled_eps(wprec, coords):
+    """WENO5's weights (Sec. 3.1.2) depend on the data through eps + IS_k,
+    and IS_k is quadratic in the data, so scaling the data by 4 and eps by 16
+    scales every eps + IS_k by 16 and leaves the weights unchanged; the
+    reduced-precision reading scales the differences to a power of two first
+    (Sec. 3.1.3), which absorbs the 4 exactly. The rest of the right-hand side
+    is linear, so F_16eps(4u) = 4 F_eps(u), and in binary floating point bit
+    for bit (powers of two commute with every rounding): the identity the
+    CUDA step's scaled second stage rests on. Multi-scale data, both
+    coordinate systems, both theta schemes."""
+    for theta_mode in (0, 1):
+        wl = (I.KERR_GRAV.with_(nr=96, nth=10) if coords == 0
+              else I.EXTREMAL_GRAV_HYP.with_(nr=120, nth=8))
+        args = (wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m)
+        g1 = o.grid(*args, eps=wl.eps, wprec=wprec, theta_mode=theta_mode, coords=wl.coords,
+                    S=wl.S)
+        g16 = o.grid(*args, eps=16.0 * wl.eps, wprec=wprec, theta_mode=theta_mode,
+                     coords=wl.coords, S=wl.S)
+        co = o.coefficients(g1)
+        u = I.multiscale_state(wl.nr, wl.nth, 21)
+        np.testing.assert_array_equal(o.rhs(g16, co, 4.0 * u), 4.0 * o.rhs(g1, co, u))
+        # and eps matters: unscaled eps on the scaled data changes the weights
+        assert np.any(o.rhs(g1, co, 4.0 * u) != 4.0 * o.rhs(g1, co, u))
+
