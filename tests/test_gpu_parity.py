@@ -167,6 +167,39 @@ def test_ssprk104_handle_graph_matches_stateless():
         T.teuk_batch_create([p])
 
 
+@pytest.mark.parametrize("theta_mode", [0, 1])
+@pytest.mark.parametrize("wprec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("coords", [0, 1])
+def test_scaled_second_stage_is_exact(coords, wprec, theta_mode):
+    """The step keeps its second SSP-RK(3,3) stage as v = 4 u^(2) and runs the
+    third on v with 16 eps and beta = 1/6. Data scaled by 4 with eps scaled by
+    16 gives the same WENO weights and, by powers of two, the same roundings,
+    so the step's result equals bit for bit the printed third stage (the
+    public single-stage call) applied to v / 4; and v / 4 is the printed second
+    stage up to its own roundings (one fewer per row). On multi-scale data
+    (rows over 1e-40..1e6, a 1e-200 tail) in both coordinate systems."""
+    wl = (I.KERR_GRAV.with_(nr=257, nth=13) if coords == 0
+          else I.EXTREMAL_GRAV_HYP.with_(nr=300, nth=10))
+    p = T.params_from_workload(wl, wprec=wprec, theta_mode=theta_mode)
+    dt = 0.5 * T.teuk_stable_dt(p)
+    coef = dev(T.teuk_build_coefficients(p, dt))
+    u0 = I.multiscale_state(wl.nr, wl.nth, 13)
+    ud = dev(u0)
+    work = torch.zeros(2, 4, wl.nth, wl.nr, dtype=torch.float64, device="cuda")
+    T.teuk_step_dev(p, dt, coef, ud, work, 1)
+    u1, w1, v = host(ud), host(work[0]), host(work[1])
+    third = torch.empty_like(ud)
+    T.teuk_stage_dev(p, dt, coef, dev(u0), dev(v / 4.0), third, 3)
+    np.testing.assert_array_equal(u1, host(third))
+    second = torch.empty_like(ud)
+    T.teuk_stage_dev(p, dt, coef, dev(u0), dev(w1), second, 2)
+    g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec,
+               theta_mode, coords=wl.coords, S=wl.S)
+    co = o.coefficients(g)
+    compare(v / 4.0, host(second), stage_scale(g, co, dt, w1, u0, 0.75, 0.25), tol=1e-14,
+            what=f"second stage {wprec}")
+
+
 def run_both(wl, wprec, nsteps, u0=None, theta_mode=0, rk=0, scheme=0):
     """nsteps on the GPU (stateless step) and in the oracle."""
     g = o.grid(wl.nr, wl.nth, wl.rs_min, wl.rs_max, wl.M, wl.a, wl.s, wl.m, wl.eps, wprec,
