@@ -242,7 +242,11 @@ teuk_status teuk_stage_dev(const teuk_params* p, double dt, const double* coef_d
  * intermediate stages) or 12*ntheta*nr for SSP-RK(10,4) (two stage registers
  * and the retained combination). dt, coef_dev as for teuk_stage_dev.
  * Asynchronous on stream; u_dev holds the state after the last step.
- * work_dev must not overlap u_dev. */
+ * work_dev must not overlap u_dev. With SSP-RK(3,3) and the WENO5 scheme the
+ * last step leaves u^(1) in the first 4 planes of work_dev and 4 u^(2) in the
+ * next 4: the second stage is kept scaled by four and the third runs on it
+ * with 16 eps, which gives the same weights and the printed third stage's
+ * roundings (Sec. 3.1.2, Sec. 3.2). */
 teuk_status teuk_step_dev(const teuk_params* p, double dt, const double* coef_dev,
                           double* u_dev, double* work_dev, int64_t nsteps,
                           void* stream);
