@@ -837,13 +837,14 @@ cudaError_t launch_batch_w(int stage, int segv, int theta, const BatchDesc* d, i
 // co-residency guarantee.
 //
 // Completion of epoch e at an item is published as flags[item] = base + e + 1
-// (a release store after a device-scope fence); a block waits for
-// flags[neighbour] >= base + e with acquire loads. The host advances `base` by
+// (a block barrier, then a release store at gpu scope by one thread); a block
+// waits for flags[neighbour] >= base + e with acquire loads, then a block
+// barrier. The host advances `base` by
 // the launch's epochs after every launch, so flags left by earlier launches
 // never satisfy a wait and nothing is cleared between launches. Each wait is
 // bounded by wait_ns of %globaltimer; when it runs out the block records the
 // item and epoch in host-mapped memory, raises `abort`, and every block stops
-// at its next check, so the launch ends and the host reports TEUK_ERR_TIMEOUT.
+// at its next spin, so the launch ends and the host reports TEUK_ERR_TIMEOUT.
 // The ticket counter and the abort word come in two copies used by alternate
 // launches (`parity`, kept by the host): block 0 of a launch zeroes the other
 // copy, which the previous launch has finished with and the next one will
@@ -886,33 +887,39 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 }
 
 // Lanes 0..8 of warp 0: wait until neighbour (rb + lane/3 - 1, sg + lane%3 - 1)
-// has completed epoch e - 1. Returns false (warp-uniform) if a wait ran out or
-// another block raised abort.
+// has completed epoch e - 1. The first acquire load usually finds it done;
+// only a wait that has to spin also watches the abort word and the time
+// bound. Returns false (warp-uniform) if a wait ran out or another block
+// raised abort. (A block whose neighbourhoods keep being ready after an abort
+// runs on to the end of its tickets: every other block stops at its next
+// spin, so the launch still ends.)
 __device__ __forceinline__ bool wait_neighbours(const FusedArgs& F, unsigned base, int e, int rb,
                                                 int sg, int item, int lane) {
-    int* abort = &F.ctl->abort[F.parity];
-    int ok = *(volatile int*)abort ? 0 : 1;
-    if (ok && e > 0 && lane < 9) {
+    int ok = 1;
+    if (e > 0 && lane < 9) {
         const int r = rb + lane / 3 - 1, g = sg + lane % 3 - 1;
         if (r >= 0 && r < F.nrb && g >= 0 && g < F.nseg) {
             const unsigned* f = F.flags + (long long)r * F.nseg + g;
             const unsigned need = base + (unsigned)e;
-            const unsigned long long t0 = global_ns();
-            for (;;) {
-                if ((int)(ld_acquire_u32(f) - need) >= 0) break;
-                if (*(volatile int*)abort) { ok = 0; break; }
-                if (global_ns() - t0 > F.wait_ns) {
-                    ok = 0;
-                    if (atomicCAS(abort, 0, 1) == 0) {
-                        volatile int* eh = F.err_host;
-                        eh[1] = e;
-                        eh[2] = item;
-                        __threadfence_system();
-                        eh[0] = 1;
+            if ((int)(ld_acquire_u32(f) - need) < 0) {
+                int* abort = &F.ctl->abort[F.parity];
+                const unsigned long long t0 = global_ns();
+                for (;;) {
+                    if (*(volatile int*)abort) { ok = 0; break; }
+                    if (global_ns() - t0 > F.wait_ns) {
+                        ok = 0;
+                        if (atomicCAS(abort, 0, 1) == 0) {
+                            volatile int* eh = F.err_host;
+                            eh[1] = e;
+                            eh[2] = item;
+                            __threadfence_system();
+                            eh[0] = 1;
+                        }
+                        break;
                     }
-                    break;
+                    __nanosleep(100);
+                    if ((int)(ld_acquire_u32(f) - need) >= 0) break;
                 }
-                __nanosleep(100);
             }
         }
     }
@@ -934,25 +941,35 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
     }
     // first ticket: the block's own index (no atomic traffic while the whole
     // grid starts); later ones from the counter, offset by the grid size
+    // first ticket: the block's own index (no atomic traffic while the whole
+    // grid starts); later ones from the counter, offset by the grid size
     unsigned long long next = blockIdx.x;
+    // Warp 0 takes the ticket (lane 0 also asks the counter for the one after
+    // it) and waits for the item's neighbourhood; one block barrier then hands
+    // the ticket and the verdict to the other warps.
     for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long t = next;
-            if ((long long)t < total) next = gridDim.x + atomicAdd(counter, 1ULL);
-            s_ticket = (long long)t;
+        if (warp == 0) {
+            long long tk = 0;
+            if (lane == 0) {
+                tk = (long long)next;
+                if (tk < total) next = gridDim.x + atomicAdd(counter, 1ULL);
+            }
+            tk = __shfl_sync(0xffffffffu, tk, 0);
+            bool go = false;
+            if (tk < total) {
+                const int e0 = (int)(tk / F.items);
+                const int it0 = (int)(tk - (long long)e0 * F.items);
+                const int rb0 = it0 / F.nseg;
+                go = wait_neighbours(F, base, e0, rb0, it0 - rb0 * F.nseg, it0, lane);
+            }
+            if (lane == 0) { s_ticket = tk; s_go = go; }
         }
         __syncthreads();
         const long long t = s_ticket;
-        if (t >= total) break;
+        if (t >= total || !s_go) break;
         const int e = (int)(t / F.items);
         const int item = (int)(t - (long long)e * F.items);
         const int rb = item / F.nseg, sg = item - rb * F.nseg;
-        if (warp == 0) {
-            const bool go = wait_neighbours(F, base, e, rb, sg, item, lane);
-            if (lane == 0) s_go = go;
-        }
-        __syncthreads();
-        if (!s_go) break;
         const int stage = e % 3 + 1;
         StageArgs A = F.A;
         // the second stage in its scaled form (kStageScaled), as in the stage launches
@@ -969,11 +986,13 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
             process_item<W, kStageScaled, THETA, SEGV, HYP, true>(A, &sm[0][0], j0, nrows, sg);
         else
             process_item<W, 2, THETA, SEGV, HYP, true>(A, &sm[0][0], j0, nrows, sg);
-        __syncthreads();            // every row's stores of this item are issued
-        if (threadIdx.x == 0 && !(F.withhold && e == 0 && item == 0)) {
-            __threadfence();
+        // Every thread's stores of this item precede the barrier; thread 0's
+        // release store at gpu scope after it makes them visible to any block
+        // that acquires the flag (a release is cumulative over what the
+        // barrier ordered before it).
+        __syncthreads();
+        if (threadIdx.x == 0 && !(F.withhold && e == 0 && item == 0))
             st_release_u32(F.flags + item, base + (unsigned)e + 1u);
-        }
     }
 }
 
