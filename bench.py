@@ -49,7 +49,7 @@ BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # sources it was taken on, identified by the sha256 of their concatenation.
 NCU_TRAFFIC = {"sources": ["paper_2010_04760_gb300/csrc/teuk_stage_kernels.cuh",
                            "paper_2010_04760_gb300/csrc/teuk_stage.cu"],
-               "sha256": "2e5fa24d77bcac0b46b1020db917d068485c36f982d2a6e5a9e4d99a659e6498",
+               "sha256": "74125ae414fa0945378688f9525139f2d11df5337b42b2ace4998d22322659db",
                "bytes_per_launch": None,
                "fused_bytes_per_launch": (31524096 + 1792 + 31525632 + 4352 + 31527168
                                           + 13824) / 3.0}

@@ -946,7 +946,7 @@ __global__ void TEUK_BOUNDS fused_step_kernel(const FusedArgs F) {
     unsigned long long next = blockIdx.x;
     // Warp 0 takes the ticket (lane 0 also asks the counter for the one after
     // it) and waits for the item's neighbourhood; one block barrier then hands
-    // the ticket and the verdict to the other warps.
+    // the ticket and the outcome of the wait to the other warps.
     for (;;) {
         if (warp == 0) {
             long long tk = 0;
