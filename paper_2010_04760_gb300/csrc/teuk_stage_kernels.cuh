@@ -203,22 +203,19 @@ __device__ __forceinline__ double f2d_exact(float f) {
 }
 
 // ---------------------------------------------------------------------------
-// Weight formats. rw() rounds a binary32 value to the format; a binary32
-// operation followed by rw() is the correctly rounded operation of the
-// format (24 >= 2p + 2 for p = 11 and p = 8).
+// Weight formats: significand bits P, smallest normal exponent EMIN, and the
+// clamp range [2^LOG2TINY, 2^LOG2HUGE] of the scaled epsilon; the arithmetic
+// of each format is Ops<W> below.
 // ---------------------------------------------------------------------------
 template <int W> struct Fmt;
 template <> struct Fmt<TEUK_W_FP32> {
     static constexpr int P = 24, EMIN = -126, LOG2TINY = -126, LOG2HUGE = 100;
-    __device__ static float rw(float x) { return x; }
 };
 template <> struct Fmt<TEUK_W_FP16> {
     static constexpr int P = 11, EMIN = -14, LOG2TINY = -14, LOG2HUGE = 15;
-    __device__ static float rw(float x) { return __half2float(__float2half_rn(x)); }
 };
 template <> struct Fmt<TEUK_W_BF16> {
     static constexpr int P = 8, EMIN = -126, LOG2TINY = -126, LOG2HUGE = 100;
-    __device__ static float rw(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 };
 
 // floor(log2 max_k |x_k|) from the bit patterns (0 if all are zero).
@@ -245,6 +242,42 @@ __device__ __forceinline__ int max_exponent(double x0, double x1, double x2, dou
     return (63 - __clzll((long long)a)) - 1074;
 }
 
+// Arithmetic of a weight format: values held in the format's own type, each
+// operation correctly rounded to nearest even in the format (the half and
+// bfloat16 instructions without contraction; a quotient taken in binary32 and
+// rounded once more is the correctly rounded quotient, 24 >= 2p + 2).
+template <int W> struct Ops;
+template <> struct Ops<TEUK_W_FP32> {
+    using T = float;
+    __device__ static T in(float x) { return x; }
+    __device__ static float out(T x) { return x; }
+    __device__ static T add(T a, T b) { return __fadd_rn(a, b); }
+    __device__ static T sub(T a, T b) { return __fsub_rn(a, b); }
+    __device__ static T mul(T a, T b) { return __fmul_rn(a, b); }
+    __device__ static T div(T a, T b) { return __fdiv_rn(a, b); }
+    __device__ static T min(T a, T b) { return fminf(a, b); }
+};
+template <> struct Ops<TEUK_W_FP16> {
+    using T = __half;
+    __device__ static T in(float x) { return __float2half_rn(x); }
+    __device__ static float out(T x) { return __half2float(x); }
+    __device__ static T add(T a, T b) { return __hadd_rn(a, b); }
+    __device__ static T sub(T a, T b) { return __hsub_rn(a, b); }
+    __device__ static T mul(T a, T b) { return __hmul_rn(a, b); }
+    __device__ static T div(T a, T b) { return in(__fdiv_rn(out(a), out(b))); }
+    __device__ static T min(T a, T b) { return __hmin(a, b); }
+};
+template <> struct Ops<TEUK_W_BF16> {
+    using T = __nv_bfloat16;
+    __device__ static T in(float x) { return __float2bfloat16_rn(x); }
+    __device__ static float out(T x) { return __bfloat162float(x); }
+    __device__ static T add(T a, T b) { return __hadd_rn(a, b); }
+    __device__ static T sub(T a, T b) { return __hsub_rn(a, b); }
+    __device__ static T mul(T a, T b) { return __hmul_rn(a, b); }
+    __device__ static T div(T a, T b) { return in(__fdiv_rn(out(a), out(b))); }
+    __device__ static T min(T a, T b) { return __hmin(a, b); }
+};
+
 // Reduced-precision Jiang-Shu weights omega_0, omega_2 (Sec. 3.1.2-3.1.3) of
 // the stencil with first differences x0..x3 (positive-direction order).
 // Smoothness indicators in first differences:
@@ -255,55 +288,51 @@ __device__ __forceinline__ int max_exponent(double x0, double x1, double x2, dou
 // to the format, epsilon by 2^-2e (clamped to [tiny, huge]), and alpha_k is
 // normalised by the smallest eps + IS: alpha_k = d_k (t_min/t_k)^2. The
 // operation sequence is fixed (no contraction) so that every rounding is
-// determined.
+// determined; each operation is one of Ops<W>, in the format itself.
 template <int W>
 __device__ __forceinline__ void reduced_weights(double x0, double x1, double x2, double x3,
                                                 const StageArgs& A, float& w0, float& w2) {
     using F = Fmt<W>;
+    using O = Ops<W>;
+    using T = typename O::T;
     const int e = max_exponent(x0, x1, x2, x3);
-    const float y0 = round_scaled_fast<F::P, F::EMIN>(x0, e);
-    const float y1 = round_scaled_fast<F::P, F::EMIN>(x1, e);
-    const float y2 = round_scaled_fast<F::P, F::EMIN>(x2, e);
-    const float y3 = round_scaled_fast<F::P, F::EMIN>(x3, e);
+    const T y0 = O::in(round_scaled_fast<F::P, F::EMIN>(x0, e));
+    const T y1 = O::in(round_scaled_fast<F::P, F::EMIN>(x1, e));
+    const T y2 = O::in(round_scaled_fast<F::P, F::EMIN>(x2, e));
+    const T y3 = O::in(round_scaled_fast<F::P, F::EMIN>(x3, e));
     // eps 2^-2e clamped to [tiny, huge], rounded to the format. Inside the
     // clamp range the value is normal in the format, so rounding it is
     // rounding eps's significand (precomputed) and shifting the exponent.
-    float eh;
+    float ehf;
     {
         const int lead = A.eps_exp - 2 * e;
-        if (lead < F::LOG2TINY) eh = pow2f(F::LOG2TINY);
+        if (lead < F::LOG2TINY) ehf = pow2f(F::LOG2TINY);
         else if (lead > F::LOG2HUGE || (lead == F::LOG2HUGE && !A.eps_pow2))
-            eh = pow2f(F::LOG2HUGE);
-        else eh = __uint_as_float(A.eps_mant + ((unsigned)lead << 23));
+            ehf = pow2f(F::LOG2HUGE);
+        else ehf = __uint_as_float(A.eps_mant + ((unsigned)lead << 23));
     }
-    const float c13 = F::rw((float)(13.0 / 12.0));
-    const float d0 = F::rw(0.1f), d1 = F::rw(0.6f), d2 = F::rw(0.3f);
-    float a, b, IS0, IS1, IS2;
-    a = F::rw(__fsub_rn(y1, y0));
-    b = F::rw(__fsub_rn(F::rw(__fmul_rn(3.0f, y1)), y0));
-    IS0 = F::rw(__fadd_rn(F::rw(__fmul_rn(c13, F::rw(__fmul_rn(a, a)))),
-                          F::rw(__fmul_rn(0.25f, F::rw(__fmul_rn(b, b))))));
-    a = F::rw(__fsub_rn(y2, y1));
-    b = F::rw(__fadd_rn(y1, y2));
-    IS1 = F::rw(__fadd_rn(F::rw(__fmul_rn(c13, F::rw(__fmul_rn(a, a)))),
-                          F::rw(__fmul_rn(0.25f, F::rw(__fmul_rn(b, b))))));
-    a = F::rw(__fsub_rn(y3, y2));
-    b = F::rw(__fsub_rn(F::rw(__fmul_rn(3.0f, y2)), y3));
-    IS2 = F::rw(__fadd_rn(F::rw(__fmul_rn(c13, F::rw(__fmul_rn(a, a)))),
-                          F::rw(__fmul_rn(0.25f, F::rw(__fmul_rn(b, b))))));
-    const float t0 = F::rw(__fadd_rn(eh, IS0));
-    const float t1 = F::rw(__fadd_rn(eh, IS1));
-    const float t2 = F::rw(__fadd_rn(eh, IS2));
-    const float tm = fminf(t0, fminf(t1, t2));
-    const float r0 = F::rw(__fdiv_rn(tm, t0));
-    const float r1 = F::rw(__fdiv_rn(tm, t1));
-    const float r2 = F::rw(__fdiv_rn(tm, t2));
-    const float a0 = F::rw(__fmul_rn(d0, F::rw(__fmul_rn(r0, r0))));
-    const float a1 = F::rw(__fmul_rn(d1, F::rw(__fmul_rn(r1, r1))));
-    const float a2 = F::rw(__fmul_rn(d2, F::rw(__fmul_rn(r2, r2))));
-    const float sum = F::rw(__fadd_rn(F::rw(__fadd_rn(a0, a1)), a2));
-    w0 = F::rw(__fdiv_rn(a0, sum));
-    w2 = F::rw(__fdiv_rn(a2, sum));
+    const T eh = O::in(ehf);
+    const T c13 = O::in((float)(13.0 / 12.0)), three = O::in(3.0f), quarter = O::in(0.25f);
+    const T d0 = O::in(0.1f), d1 = O::in(0.6f), d2 = O::in(0.3f);
+    T a, b, IS0, IS1, IS2;
+    a = O::sub(y1, y0);
+    b = O::sub(O::mul(three, y1), y0);
+    IS0 = O::add(O::mul(c13, O::mul(a, a)), O::mul(quarter, O::mul(b, b)));
+    a = O::sub(y2, y1);
+    b = O::add(y1, y2);
+    IS1 = O::add(O::mul(c13, O::mul(a, a)), O::mul(quarter, O::mul(b, b)));
+    a = O::sub(y3, y2);
+    b = O::sub(O::mul(three, y2), y3);
+    IS2 = O::add(O::mul(c13, O::mul(a, a)), O::mul(quarter, O::mul(b, b)));
+    const T t0 = O::add(eh, IS0), t1 = O::add(eh, IS1), t2 = O::add(eh, IS2);
+    const T tm = O::min(t0, O::min(t1, t2));
+    const T r0 = O::div(tm, t0), r1 = O::div(tm, t1), r2 = O::div(tm, t2);
+    const T a0 = O::mul(d0, O::mul(r0, r0));
+    const T a1 = O::mul(d1, O::mul(r1, r1));
+    const T a2 = O::mul(d2, O::mul(r2, r2));
+    const T sum = O::add(O::add(a0, a1), a2);
+    w0 = O::out(O::div(a0, sum));
+    w2 = O::out(O::div(a2, sum));
 }
 
 // 6 (fhat_{i+1/2} - f_i) for first differences x0..x3 (positive-direction
