@@ -209,10 +209,10 @@ def time_gpu_steps(T, torch, wprec, steps, warmup, stream, flush, launch=None):
 def waveform_error(T, torch, stream, t_end=WL.t_end, r_ext=50.0):
     """Relative L2 difference of the waveform (Psi at r* = r_ext over all theta,
     sampled every 100 steps up to t_end, the workload's stated duration of
-    500 M) between binary32 and binary64 weights."""
+    500 M) between each reduced weight format and binary64 weights."""
     waves = {}
     t = 0.0
-    for wprec in ("fp64", "fp32"):
+    for wprec in ("fp64", "fp32", "fp16", "bf16"):
         h = T.teuk_create(T.params_from_workload(WL, wprec=wprec), stream)
         T.teuk_set_state(h, I.initial_data(WL), 0.0)
         _, dt, _ = T.teuk_get_info(h)
@@ -223,8 +223,9 @@ def waveform_error(T, torch, stream, t_end=WL.t_end, r_ext=50.0):
         _, dt, t = T.teuk_get_info(h)
         h.close()
         waves[wprec] = np.array(ws)
-    err = np.linalg.norm(waves["fp32"] - waves["fp64"]) / np.linalg.norm(waves["fp64"])
-    return float(err), t
+    ref = np.linalg.norm(waves["fp64"])
+    errs = {w: float(np.linalg.norm(waves[w] - waves["fp64"]) / ref) for w in ("fp32", "fp16", "bf16")}
+    return errs, t
 
 
 def time_multi_step(T, torch, wprec, steps, warmup, stream, flush):
@@ -553,7 +554,8 @@ def main():
             "value": 3.3, "what": "binary128 state with binary64 weights vs all-binary128, "
             "WENO5 in rho, 16384 x 64 (Sec. 4-5)", "hardware": "not stated in the paper "
             "(its GPU runs use V100 nodes)", "comparable": False},
-        "waveform_rel_l2_fp32_vs_fp64_weights": err,
+        "waveform_rel_l2_fp32_vs_fp64_weights": err["fp32"],
+        "waveform_rel_l2_vs_fp64_weights": err,
         "waveform_error_window": f"Psi(r*=50M, all theta) every 100 steps to t={t_err:.1f}M",
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_derived,
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak_derived,
