@@ -346,7 +346,8 @@ teuk_status teuk_step(teuk_handle* h, int64_t nsteps);
 /* Launch mode of teuk_step (teuk_launch) and the bound of each device-side
  * wait of the fused step in seconds, wait_seconds in [1e-6, 3600] (default 2:
  * a wait lasts about one work item, tens of microseconds, when all is well).
- * A wait that runs out makes every block of the launch stop; the next call
+ * A wait that runs out makes the launch end (every block stops at its next
+ * wait that cannot be met at once); the next call
  * that synchronises the handle's stream (teuk_synchronize, teuk_observe,
  * teuk_get_state, teuk_set_state, teuk_check_finite) or the next teuk_step
  * returns TEUK_ERR_TIMEOUT, and the state is then undefined (restore it with
