@@ -11,6 +11,10 @@ Layout: state ``u[4, nth, nr]`` (Psi_R, Psi_I, pi_R, pi_I); coefficients
 (c: the pi rows' speed, equal to b in r*). Radial coordinate: r* (coords 0) or
 the hyperboloidal rho (coords 1), its range in ``rs_min, rs_max`` either way.
 Weight precision codes: 0 binary64, 1 binary32, 2 binary16, 3 bfloat16.
+
+``ld_rhs`` / ``ld_rk3_step`` (``teuk_oracle_ld.c``) evolve the same discrete
+problem with the state in C long double, to measure the binary64 state's own
+round-off.
 """
 import ctypes
 import os
