@@ -149,9 +149,13 @@ def dist_init(gpus):
     ranks of the timed region: the replicas exchange no data."""
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
+        import datetime
         import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        # a rank that dies or never arrives ends the others' next collective
+        # with an error after this long instead of the library default (30 min)
+        timeout = datetime.timedelta(seconds=float(os.environ.get("TEUK_PG_TIMEOUT_S", "600")))
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo", timeout=timeout)
     return rank, world
 
 

@@ -93,3 +93,41 @@ def test_reference_arm_under_torchrun_prints_from_rank_0_only():
     assert out.returncode == 0, out.stderr[-3000:]
     lines = _json_lines(out.stdout)
     assert len(lines) == 1 and lines[0]["n_gpus"] == 2
+
+
+def _rank_failing(rank, world, port, outdir):
+    """Rank 1 leaves before the barrier (between steps, nothing in flight);
+    rank 0 must learn of it from the collective, within the group timeout."""
+    import time
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), TEUK_PG_TIMEOUT_S="20")
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.dist_init(world)
+    if rank == 1:
+        os._exit(0)
+    t0 = time.time()
+    try:
+        bench.barrier(world)
+        bench.max_over_ranks(1.0, world, torch.device("cpu"))
+        outcome = "completed"
+    except Exception as e:                                  # noqa: BLE001
+        outcome = "raised: " + type(e).__name__
+    with open(os.path.join(outdir, "rank0.json"), "w") as fh:
+        json.dump({"outcome": outcome, "seconds": time.time() - t0}, fh)
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_ends_the_others_collective_with_an_error(tmp_path):
+    mp = torch.multiprocessing.get_context("spawn")
+    port = _free_port()
+    procs = [mp.Process(target=_rank_failing, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+        assert p.exitcode == 0
+    res = json.load(open(tmp_path / "rank0.json"))
+    assert res["outcome"].startswith("raised"), res
+    assert res["seconds"] < 60, res
+
