@@ -130,3 +130,73 @@ def test_the_model_detects_a_missing_neighbour_wait():
     with pytest.raises(AssertionError):
         for seed in range(20):
             simulate(2, 3, 3, 6, seed, wait_reach=0)
+
+
+def simulate_withheld(nrb, nseg, steps, blocks, seed, wait_bound=4.0):
+    """The same schedule with item 0's first completion never published (the
+    kernel's test hook) and the kernel's wait rules: a block takes its ticket,
+    reads the neighbours' flags, and if one is not yet set spins until it is,
+    until another block has raised the abort word (then it stops), or until
+    its own wait has lasted wait_bound (then it raises abort and stops); a
+    block whose neighbourhood is ready computes whatever the abort word says.
+    Returns (items completed, blocks that stopped on abort, abort raised)."""
+    rng = np.random.default_rng(seed)
+    items = nrb * nseg
+    total = items * 3 * steps
+    done_at = {}
+
+    def nbrs(item):
+        rb, sg = divmod(item, nseg)
+        for dr in (-1, 0, 1):
+            for ds in (-1, 0, 1):
+                r, g = rb + dr, sg + ds
+                if 0 <= r < nrb and 0 <= g < nseg:
+                    yield r * nseg + g
+
+    next_ticket = blocks
+    events = [(0.0, b, b, None) for b in range(blocks)]    # (time, block, ticket, spin start)
+    heapq.heapify(events)
+    abort = None
+    completed = stopped = 0
+    guard = 0
+    while events:
+        guard += 1
+        assert guard < 100 * total + 10 * blocks, "schedule did not end"
+        now, b, t, spin0 = heapq.heappop(events)
+        if t >= total:
+            continue
+        e, item = divmod(t, items)
+        need = [] if e == 0 else [done_at.get((e - 1, n)) for n in nbrs(item)]
+        if any(x is None or x > now for x in need):
+            if spin0 is None:
+                spin0 = now
+            if abort is not None and abort <= now:
+                stopped += 1
+                continue
+            if now >= spin0 + wait_bound:
+                abort = now if abort is None else abort
+                stopped += 1
+                continue
+            known = [x for x in need if x is not None and x > now]
+            wake = min(known + [spin0 + wait_bound, now + 0.25])
+            heapq.heappush(events, (wake, b, t, spin0))
+            continue
+        fin = now + rng.uniform(0.5, 1.5)
+        if not (e == 0 and item == 0):                     # the withheld flag
+            done_at[(e, item)] = fin
+        completed += 1
+        heapq.heappush(events, (fin, b, next_ticket, None))
+        next_ticket += 1
+    return completed, stopped, abort is not None
+
+
+@pytest.mark.parametrize("nrb,nseg,steps,blocks", [(4, 4, 3, 5), (6, 9, 4, 16), (8, 8, 2, 200)])
+def test_a_withheld_flag_ends_the_launch(nrb, nseg, steps, blocks):
+    """Every block ends: the waits that depend on the withheld flag run out,
+    raise abort, and every block that then has to wait stops, while work whose
+    neighbourhood is ready may still finish; the launch ends early."""
+    for seed in range(3):
+        completed, stopped, aborted = simulate_withheld(nrb, nseg, steps, blocks, seed)
+        assert aborted
+        assert 0 < completed < nrb * nseg * 3 * steps
+        assert stopped >= 1
