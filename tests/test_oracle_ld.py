@@ -94,13 +94,20 @@ def _closed_form_rhs(g, co, ab):
     return F, np.broadcast_to(S, F.shape)
 
 
-@pytest.mark.parametrize("a,s,m", [(0.9, -2, 2), (0.0, 0, 0), (0.5, -1, 1)])
-def test_rhs_of_linear_state_in_closed_form(a, s, m):
-    """The extended right-hand side of a row-constant state linear in r*
-    matches its closed form to 8 units of the long double format of the
-    terms' size at nodes whose stencils stay inside the grid; the binary64
-    oracle on the same state (rounded to binary64) does not."""
-    g = o.grid(96, 6, -30.0, 60.0, 1.0, a, s, m)
+@pytest.mark.parametrize("a,s,m,coords", [(0.9, -2, 2, 0), (0.0, 0, 0, 0), (0.5, -1, 1, 0),
+                                          (1.0, -2, 0, 1), (0.7, 0, 2, 1)])
+def test_rhs_of_linear_state_in_closed_form(a, s, m, coords):
+    """The extended right-hand side of a row-constant state linear in the
+    radial index (r*, or rho on the hyperboloidal slices, whose pi rows move
+    with their own speed c) matches its closed form to 8 units of the long
+    double format of the terms' size at nodes whose stencils stay inside the
+    grid; the binary64 oracle on the same state (rounded to binary64) does
+    not."""
+    if coords == 1:
+        rho_p = o.horizon_rho(1.0, a, 20.0)
+        g = o.grid(96, 6, rho_p + 0.5, 15.0, 1.0, a, s, m, coords=1, S=20.0)
+    else:
+        g = o.grid(96, 6, -30.0, 60.0, 1.0, a, s, m)
     co = o.coefficients(g)
     u, ab = _linear_state(g.nr, g.nth, seed=11)
     ex, S = _closed_form_rhs(g, co, ab)
@@ -110,8 +117,7 @@ def test_rhs_of_linear_state_in_closed_form(a, s, m):
     bound = 8 * EPS_LD * S[..., inner]
     assert np.all(err <= bound), float(np.max(err / bound))
     # the same bound is beyond binary64 arithmetic
-    got_d = o.rhs(o.grid(96, 6, -30.0, 60.0, 1.0, a, s, m, wprec="fp64"), co,
-                  u.astype(np.float64))
+    got_d = o.rhs(g, co, u.astype(np.float64))
     err_d = np.abs((got_d.astype(L) - ex)[..., inner]).astype(np.float64)
     assert np.max(err_d / bound) > 64
 
