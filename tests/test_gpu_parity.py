@@ -76,6 +76,33 @@ def test_operator_parity(wprec, shape, phys, theta_mode):
                 what=f"{wprec} {shape} {phys} theta={theta_mode} smooth={smooth}")
 
 
+@pytest.mark.parametrize("theta_mode", [0, 1])
+@pytest.mark.parametrize("wprec,step,period", [("fp16", 6, 6), ("bf16", 33, 5), ("fp32", 33, 5)])
+def test_operator_parity_where_reduced_weights_underflow(wprec, step, period, theta_mode):
+    """Radial lines whose magnitudes fall by 2^-step from node to node
+    (repeating every `period` nodes, random signs and 10% jitter): within a
+    stencil the scaled first differences, their squares and the ratios of the
+    weights reach the format's subnormal range, where every operation must
+    still round as the oracle's emulation does (gradual underflow, no flush
+    to zero) for the weights to agree bit for bit."""
+    nr, nth = 190, 6
+    rng = np.random.default_rng(17)
+    mag = np.exp2(-step * (np.arange(nr) % period).astype(float))
+    u = np.empty((4, nth, nr))
+    for c in range(4):
+        for j in range(nth):
+            u[c, j] = mag * rng.choice([-1.0, 1.0], nr) * (1.0 + 0.1 * rng.random(nr))
+    g = o.grid(nr, nth, -40.0, 120.0, 1.0, 0.9, -2, 2, 1e-6, wprec, theta_mode)
+    co = o.coefficients(g)
+    F = o.rhs(g, co, u)
+    p = T.make_params(nr, nth, -40.0, 120.0, 1.0, 0.9, -2, 2, wprec=wprec, theta_mode=theta_mode)
+    coef = dev(T.teuk_build_coefficients(p, 1.0))
+    out = torch.empty(4, nth, nr, dtype=torch.float64, device="cuda")
+    T.teuk_stage_dev(p, 1.0, coef, None, dev(u), out, 0)
+    compare(host(out), F, stage_scale(g, co, 1.0, u, with_prev=False),
+            what=f"{wprec} underflowing stencils theta={theta_mode}")
+
+
 @pytest.mark.parametrize("wprec", ["fp64", "fp32"])
 def test_rk_stages_parity(wprec):
     nr, nth, a, s, m = 300, 20, 0.9, -2, 1
