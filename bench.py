@@ -49,7 +49,7 @@ BYTES_PER_PT_STAGE = 88.0 + 32.0 + 32.0 + 32.0 * 2.0 / 3.0
 # sources it was taken on, identified by the sha256 of their concatenation.
 NCU_TRAFFIC = {"sources": ["paper_2010_04760_gb300/csrc/teuk_stage_kernels.cuh",
                            "paper_2010_04760_gb300/csrc/teuk_stage.cu"],
-               "sha256": "fff3a1c91f36bc5a39e912a2e5f0706bd6079b90619d42490c62bc01941a54f4",
+               "sha256": "8f707ed7140000abda869bfac7c57a7e66cadbd2f78163b16bd1f1cae006ad7a",
                "bytes_per_launch": None,
                "fused_bytes_per_launch": (31525376 + 5632 + 31525632 + 22784 + 31526144
                                           + 11008) / 3.0}

@@ -1,12 +1,14 @@
 #pragma once
 // Fused WENO5 / Teukolsky right-hand side / Runge-Kutta stage kernel for
 // sm_103a (SSP-RK(3,3) stages, or the forward-Euler stages of SSP-RK(10,4)):
-// the device code, shared by teuk_stage.cu (r* kernels, batches, launch code)
-// and teuk_stage_hyp.cu (the hyperboloidal instantiations, compiled in
-// parallel).
+// the device code, shared by teuk_stage.cu (r* kernels, batches, launch code),
+// teuk_stage_hyp.cu (the hyperboloidal instantiations) and teuk_fused.cu /
+// teuk_fused_hyp.cu (the fused persistent step), compiled in parallel.
 //
-// One warp owns a segment of SEG consecutive radial nodes (r*, or rho on the
-// hyperboloidal slices) of one theta row. It
+// A work item is a segment of SEG consecutive radial nodes (r*, or rho on the
+// hyperboloidal slices) of WARPS theta rows, one row per warp. The block's
+// threads share phases 1-3 over the item's rows (process_item), and each warp
+// then does phase 4 for its own row:
 //   1. forms the binary64 first differences d_k = f_{k+1} - f_k of the four
 //      components over the segment plus its halo (ghosts copy the edge value
 //      in r*; on the hyperboloidal slices they extrapolate the quartic
@@ -23,9 +25,9 @@
 //      rows move with their own speed c on the hyperboloidal slices) and the
 //      Runge-Kutta combination (Sec. 3.2), and stores the new stage.
 // Every binary64 quantity is formed once per node (no recomputation inside a
-// segment); the weights run on the FP32 pipes. The only binary64 operations
-// are the differences, the weighted flux combination, the right-hand side and
-// the Runge-Kutta update.
+// segment); the weights run in their format's own arithmetic, off the FP64
+// pipe. The only binary64 operations are the differences, the weighted flux
+// combination, the right-hand side and the Runge-Kutta update.
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
