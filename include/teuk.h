@@ -276,8 +276,12 @@ teuk_status teuk_step_dev_static(const teuk_params* p, double dt, const double* 
 
 /* ---- handle API (library-owned device memory) --------------------------- */
 
-/* Allocate the state, stage buffers and coefficient array on the current
- * device and build the coefficients (teuk_stable_dt when p->dt == 0).
+/* One evolution of the paper's problem: the Teukolsky equation of spin
+ * weight s for the azimuthal mode m on a Kerr black hole of mass M and spin a
+ * (Eq. teuk0, Sec. 2), in first-order form (Eq. evln, Sec. 2.3), on the
+ * (x, theta) grid of p (Sec. 3). Allocate the state, stage buffers and
+ * coefficient array on the current device and build the coefficients
+ * (teuk_stable_dt when p->dt == 0).
  * stream: the CUDA stream every later call of this handle runs on; NULL
  * creates a non-blocking stream that teuk_destroy destroys.
  * The state starts at zero, t = 0. */
@@ -329,7 +333,9 @@ teuk_status teuk_get_state_async(teuk_handle* h, double* u_host);
 /* Wait until everything enqueued on the handle's stream has completed. */
 teuk_status teuk_synchronize(teuk_handle* h);
 
-/* Advance nsteps steps of p's integrator. With the fused step (by default
+/* Advance nsteps steps of p's integrator (Sec. 3.2: SSP-RK(3,3) or
+ * SSP-RK(10,4); every stage the WENO5 operator of Sec. 3.1, or the FD6 + KO8
+ * scheme of Sec. 3.1.1, and the right-hand side of Eq. evln). With the fused step (by default
  * for SSP-RK(3,3) with WENO5 when the grid has at least as many work items
  * per stage as resident blocks; see teuk_set_launch) one persistent launch
  * runs
